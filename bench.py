@@ -1,0 +1,302 @@
+"""Benchmark: converged RPM-FFT solves per second on the 128^3 near-void cell.
+
+One step = one cold-start RPM-FFT solve (Algorithm 2) to the fixed-point
+increment tolerance 1e-6 of the 128^3 near-void cell (RSA spheres of radius
+6-12 voxels, E = 1e-6, 20 % volume fraction, matrix E = 1, nu = 0.3,
+C0 = matrix moduli, macroscopic strain e1 (x) e1, p_max = 20, n_max = 10),
+through the C ABI on the library's CUDA kernels.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank solves its own seeded cell (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.  `--impl
+reference` times the FP64 CPU oracle on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import microstructure as ms  # noqa: E402
+
+METRIC = "converged RPM-FFT solves/s at 128^3, tol 1e-6"
+UNIT = "solves/s"
+N = 128
+TOL = 1e-6
+P_MAX = 20
+BYTES_PER_VOXEL_GAMMA = 49          # read eps 24 B + phase 1 B, write xi 24 B
+L2_FLUSH_BYTES = 256 << 20
+
+
+def workload_config(extra: dict | None = None) -> dict:
+    cfg = {"workload": "nearvoid128: RPM-FFT solve, 128^3 cell, RSA spheres r 6-12 vox, E_incl 1e-6,"
+                       " vf 0.20, C0 = matrix, E = e1(x)e1, tol 1e-6, p_max 20, n_max 10",
+           "grid": [N, N, N], "tol": TOL, "p_max": P_MAX, "n_max": 10, "c0_scale": 1.0,
+           "load": "e11", "precision": "fp32 fields, fp64 reductions/QR/Newton",
+           "l2": "flushed before every timed step (256 MiB write)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_sample(cell, iters_sample: int = 2) -> dict:
+    """Time the FP64 oracle on a bounded sample of the workload: the first
+    `iters_sample` RPM iterations (plus the initial F) of the same solve."""
+    from oracle import rpm_oracle as o
+    prob = o.Problem.from_cell(cell)
+    E = ms.unit_strain(0)
+    o.apply_F(prob, o.uniform(E, prob.shape), E)       # builds the Green cache, not timed
+    t0 = time.perf_counter()
+    r = o.rpm_solve(prob, E, o.Options(tol=TOL, p_max=P_MAX, max_iters=iters_sample))
+    dt = time.perf_counter() - t0
+    return {"seconds": dt, "f_applies": r.f_applies, "sec_per_f": dt / max(r.f_applies, 1)}
+
+
+def oracle_reference_iters() -> int | None:
+    p = os.path.join(ROOT, "tests", "golden", "nearvoid128_oracle_solve.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return int(json.load(f)["f_applies"])
+    return None
+
+
+def run_reference(args):
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return
+    cell = ms.cell_nearvoid(N, 0, c0_scale=1.0)
+    nF = oracle_reference_iters()
+    times = []
+    for i in range(args.warmup + args.steps):
+        s = oracle_sample(cell, 1)
+        if i >= args.warmup:
+            times.append(s["sec_per_f"])
+    sec_per_f = statistics.median(times)
+    f_per_solve = nF if nF else None
+    value = 1.0 / (sec_per_f * f_per_solve) if f_per_solve else None
+    sample = (f"each step: oracle RPM solve of the 128^3 cell bounded to 1 iteration "
+              f"(2 F applications); solves/s = 1 / (median s per F x {f_per_solve} F per "
+              f"converged oracle solve, tests/golden/nearvoid128_oracle_solve.json)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_per_f * 1e3 * 2,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__ as entry
+    entry.build()
+    from paper_2003_07720_gb300 import rpm
+
+    cell = ms.cell_nearvoid(N, rank, c0_scale=1.0)
+    E = ms.unit_strain(0)
+    opts = rpm.rpm_default_options(tol=TOL, p_max=P_MAX, n_max=10, profile=1)
+    stream = torch.cuda.current_stream()
+    ctx = rpm.Context(cell, opts, stream=stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    eps_out = torch.empty((6, N, N, N), dtype=torch.float32, device="cuda")
+
+    for _ in range(args.warmup):
+        ctx.solve(E, eps_out=eps_out)
+
+    sampler = ClockSampler(local)
+    if rank == 0:
+        sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    infos = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        st, info = ctx.solve(E, eps_out=eps_out)
+        ev[k][1].record(stream)
+        infos.append(info)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop() if rank == 0 else None
+    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    t = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    dev_ms_max = float(t.item())
+    value = world * args.steps / (dev_ms_max / 1e3)
+
+    # dominant kernel class and its roofline (device times from CUDA events
+    # recorded by the library on this stream during the timed steps)
+    gamma_ms = sum(i["gamma_ms"] for i in infos)
+    n_gamma = sum(i["gamma_applies"] for i in infos)
+    proj_ms = sum(i["proj_ms"] for i in infos)
+    launches = sum(i["launches"] for i in infos)
+    pk = peaks()
+    t_gamma = gamma_ms / max(n_gamma, 1) / 1e3
+    alg_bytes = BYTES_PER_VOXEL_GAMMA * N ** 3
+    achieved = alg_bytes / t_gamma / 1e9
+    roofline = {"bound": "hbm", "kernel": "gamma_apply (pass A+B+C, one F application)",
+                "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": None,
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "avg_launch_ms": round(t_gamma * 1e3, 4), "peak_src": pk["src"],
+                "time_share": {"gamma_ms": round(gamma_ms, 3), "projection_ms": round(proj_ms, 3),
+                               "solve_ms": round(dev_ms, 3)}}
+
+    # end to end through the C ABI with host buffers: phase map in, strain field out
+    phase_host = np.ascontiguousarray(cell.phase)
+    out_host = torch.empty((6, N, N, N), dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    e2e_t = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rpm.rpm_set_phase(ctx.handle, phase_host)
+        st, info = ctx.solve(E, eps_out=out_host, out_on_host=True)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = sum(e2e_t)
+    t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    e2e_value = world * args.steps / float(t.item())
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        s = oracle_sample(cell, 1)
+        nF_gpu = statistics.median(i["gamma_applies"] for i in infos)
+        cpu = {"value": 1.0 / (s["sec_per_f"] * nF_gpu), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"oracle RPM solve of this cell bounded to 1 iteration ({s['f_applies']} F "
+                         f"applications, {s['seconds']:.1f} s on 1 host core); scaled by the "
+                         f"{nF_gpu:g} F applications of the converged GPU solve"}
+    ctx.close()
+    if rank == 0:
+        it = [i["iters"] for i in infos]
+        pb = [i["basis_size"] for i in infos]
+        line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(dev_ms_max / args.steps, 3), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic (seeded RSA near-void cell per rank)",
+                "config": workload_config({"iters": it, "basis_size": pb,
+                                           "gamma_applies": [i["gamma_applies"] for i in infos],
+                                           "residual": [i["residual"] for i in infos],
+                                           "parallelism": f"replicas x{world}"}),
+                "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": {"value": round(e2e_value, 3), "unit": UNIT,
+                        "h2d_bytes_per_step": int(phase_host.nbytes) + 48,
+                        "d2h_bytes_per_step": int(out_host.numel() * 4)},
+                "gpu_launches": int(launches), "clocks": clocks, "wall_s": round(wall, 3)}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,173 @@
+/*
+ * rpm.h - C ABI of the GB300 RPM-FFT library.
+ *
+ * The library computes the strain and stress fields and the effective
+ * stiffness of a periodic, voxelised, linear-elastic cell with isotropic
+ * phases, by the fixed-point Lippmann-Schwinger scheme (Moulinec-Suquet,
+ * Section 2 and Algorithm 1 of Peng, Nepal & Dayal, CMAME 2020) wrapped by
+ * the recursive projection method (Section 3, Algorithm 2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - A grid is nx * ny * nz voxels (x fastest), unit cell lengths lx, ly, lz.
+ *   This build supports nx == ny in {4, 8, 16, 32, 64, 128} and
+ *   nz in {1, 2, 4, ..., 256}; nz = 1 is a 2D plane-strain cell.  Other
+ *   grids return RPM_ERR_UNSUPPORTED_GRID.
+ * - A field is float32 [6][nz][ny][nx]: the symmetric tensor components
+ *   11, 22, 33, 23, 13, 12 (tensor components, not engineering shears).
+ *   Field pointers are DEVICE pointers unless an argument says otherwise,
+ *   16-byte aligned, owned by the caller, and used in order on the stream
+ *   given to rpm_create.
+ * - A macroscopic strain E[6] is given in the same tensor components.
+ * - The effective stiffness is a 6x6 Voigt matrix with engineering shear
+ *   strains (row-major, order 11 22 33 23 13 12).
+ * - Every call returns an rpm_status; on failure rpm_last_error() gives a
+ *   message.  No call throws across the ABI.  A context is not thread-safe.
+ */
+#ifndef RPM_H
+#define RPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rpm_ctx rpm_ctx;
+
+typedef enum {
+  RPM_OK = 0,
+  RPM_ERR_INVALID_ARG = 1,      /* null pointer, bad size, bad option */
+  RPM_ERR_UNSUPPORTED_GRID = 2, /* grid outside the supported set above */
+  RPM_ERR_OOM = 3,              /* device allocation failed or exceeds the cap */
+  RPM_ERR_CUDA = 4,             /* a CUDA call failed; see rpm_last_error */
+  RPM_ERR_NOT_CONVERGED = 5,    /* max_iters reached above tolerance */
+  RPM_ERR_DIVERGED = 6,         /* residual non-finite or grew past the bound */
+  RPM_ERR_TIMEOUT = 7           /* reserved for bounded device waits */
+} rpm_status;
+
+typedef struct {
+  int nx, ny, nz;
+  double lx, ly, lz; /* cell lengths; 0 means 1 */
+} rpm_grid;
+
+/* Isotropic moduli: C_ijkl = lambda d_ij d_kl + mu (d_ik d_jl + d_il d_jk). */
+typedef struct {
+  double lambda, mu;
+} rpm_iso;
+
+enum { RPM_NYQ_ZERO_MIXED = 0, RPM_NYQ_SIGNED = 1 };
+
+typedef struct {
+  int n_max;             /* fixed-point steps between basis growths (Alg. 2), default 10 */
+  int p_max;             /* cap on the unstable-basis size; 0 = basic scheme (Alg. 1); <= 32 */
+  int max_iters;         /* fixed-point steps before RPM_ERR_NOT_CONVERGED, default 5000 */
+  double tol;            /* stop when |F(eps) - eps| / (|E| sqrt(n)) <= tol, default 1e-6 */
+  double t_ratio;        /* kappa: add one vector when |T22| <= kappa |T11| (Eq. 3.8), 0.1 */
+  int nyquist;           /* RPM_NYQ_ZERO_MIXED (default) or RPM_NYQ_SIGNED */
+  double diverge_factor; /* RPM_ERR_DIVERGED when residual > factor * initial, 1e10 */
+  double max_device_gb;  /* refuse contexts needing more device memory; 0 = no cap */
+  int profile;           /* 1: time Gamma0 applications and projections with CUDA events */
+} rpm_options;
+
+typedef struct {
+  int iters;           /* fixed-point steps taken */
+  int gamma_applies;   /* applications of the Gamma0 map, including F_u z for H */
+  int basis_size;      /* final size p of the unstable basis Z */
+  int converged;       /* 1 if the residual met tol */
+  int status;          /* rpm_status of the solve */
+  double residual;     /* final fixed-point increment residual */
+  double residual0;    /* residual of the initial guess */
+  double mean_stress[6]; /* <sigma> of the returned strain field (FP64 sum) */
+  float ms;            /* device time of the solve (CUDA events), milliseconds */
+  float gamma_ms;      /* with opt.profile: summed device time of the Gamma0 applications */
+  float proj_ms;       /* with opt.profile: summed time of the projection/combine kernels */
+  long long launches;  /* CUDA kernels launched by the solve */
+} rpm_solve_info;
+
+/* Fill `opt` with the defaults listed above. */
+void rpm_default_options(rpm_options* opt);
+
+/*
+ * Create a context for one cell (Section 2: the periodic cell problem with
+ * stiffness C(x) and reference medium C0, Eqs. 2.1-2.3).
+ *   grid        grid and cell lengths.
+ *   phase       uint8 phase id per voxel [nz][ny][nx], each < n_phases;
+ *               a device pointer if phase_on_device, else a host pointer.
+ *               Copied; the caller keeps ownership.
+ *   phases      n_phases (1..256) isotropic moduli, host array, copied.
+ *   c0          reference medium, lambda0 + 2 mu0 > 0, mu0 > 0.
+ *   opt         options (may be NULL for defaults), copied.
+ *   cuda_stream cudaStream_t for every later call (NULL: legacy stream).
+ * The context owns its device buffers: the half spectrum, strain
+ * iterates, the fixed-point history, the basis Z and F_u Z (p_max fields each).
+ */
+rpm_status rpm_create(const rpm_grid* grid, const uint8_t* phase, int phase_on_device,
+                      int n_phases, const rpm_iso* phases, rpm_iso c0, const rpm_options* opt,
+                      void* cuda_stream, rpm_ctx** out);
+
+/* Replace the phase map (same grid); host or device pointer as flagged. */
+rpm_status rpm_set_phase(rpm_ctx* ctx, const uint8_t* phase, int on_device);
+
+/* Replace the options (p_max may not exceed the value given at creation). */
+rpm_status rpm_set_options(rpm_ctx* ctx, const rpm_options* opt);
+
+enum {
+  RPM_GAMMA_FULL_MAP = 0, /* out = F(in) = E - Gamma0 * ((C - C0) : in), Eq. 3.9, 2.4-2.5 */
+  RPM_GAMMA_LINEAR = 1,   /* out = F_u in = -Gamma0 * ((C - C0) : in)  (E ignored) */
+  RPM_GAMMA_RAW_TAU = 2   /* out = -Gamma0 * in, `in` being a polarization tau (E ignored) */
+};
+
+/*
+ * One application of the Lippmann-Schwinger fixed-point map (Eq. 3.9 in
+ * polarization form; Eqs. 2.3-2.5): polarization, forward 3D real FFT,
+ * Green operator of C0 per frequency (zero frequency set to E, mixed
+ * Nyquist frequencies per opt.nyquist), inverse FFT.
+ *   in, out  device fields [6][n]; may not alias.  E: host double[6].
+ * Stream-ordered, asynchronous; uses the context's spectrum scratch.
+ */
+rpm_status rpm_apply_gamma(rpm_ctx* ctx, const float* in, const double E[6], float* out,
+                           int flags);
+
+/*
+ * Solve the cell problem for macroscopic strain E (Algorithm 2; Algorithm 1
+ * when p_max = 0).
+ *   E          host double[6].
+ *   eps0       optional device field, initial strain (NULL: eps0 = E).
+ *   eps_out    optional output strain field; sig_out optional stress field.
+ *   out_on_host  0: eps_out/sig_out are device pointers; 1: host pointers.
+ *   info       optional; filled also on failure.
+ * Synchronises the context stream before returning.
+ */
+rpm_status rpm_solve(rpm_ctx* ctx, const double E[6], const float* eps0, float* eps_out,
+                     float* sig_out, int out_on_host, rpm_solve_info* info);
+
+/*
+ * Effective stiffness: six solves with the unit Voigt strains (shears as
+ * engineering strain 1, i.e. eps_ij = eps_ji = 1/2); column j of C_eff is
+ * <sigma> of load j.  C_eff: host double[36] row-major; info: optional
+ * host array of 6.
+ */
+rpm_status rpm_effective_stiffness(rpm_ctx* ctx, double C_eff[36], rpm_solve_info info[6]);
+
+/* Last error message of the context (never NULL). */
+const char* rpm_last_error(const rpm_ctx* ctx);
+
+/* Name of a status code. */
+const char* rpm_status_string(rpm_status s);
+
+/* Device bytes held by the context. */
+size_t rpm_device_bytes(const rpm_ctx* ctx);
+
+/* 1 if the grid is supported by this build, else 0. */
+int rpm_grid_supported(int nx, int ny, int nz);
+
+/* Release every resource of the context (NULL is allowed). */
+void rpm_destroy(rpm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RPM_H */

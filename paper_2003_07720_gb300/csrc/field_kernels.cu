@@ -1,0 +1,314 @@
+// Field-wide kernels around the fixed-point map: the inner products and
+// tall-skinny projections of the recursive projection method (Section 3,
+// Eqs. 3.10-3.13), the Newton step on the unstable subspace, the strain
+// combine of Algorithm 2 and the constitutive law sigma = C(x) : eps.
+//
+// Fields are [6][n] float32 (components 11 22 33 23 13 12).  The inner
+// product is the tensor Frobenius product (weights 1,1,1,2,2,2).  Each
+// thread accumulates a bounded number of products in float32; the block and
+// grid reductions run in float64 with a fixed order (deterministic).
+#include <math.h>
+
+#include "rpm_internal.h"
+
+namespace rpm {
+
+constexpr int kRedThreads = 256;
+constexpr int kPerThread = 8;        // float4 per thread per dot pass (32 products)
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-reduce M float values per thread (acc) into partials[j * nblk + blockIdx.x].
+template <int M>
+__device__ __forceinline__ void block_store(const float* acc, int m, double* partials, int nblk) {
+  __shared__ double red[kRedThreads / 32][M];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    if (j < m) {
+      const double s = warp_sum((double)acc[j]);
+      if (lane == 0) red[warp][j] = s;
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kRedThreads / 32; ++w) s += red[w][j];
+    partials[(size_t)j * nblk + blockIdx.x] = s;
+  }
+}
+
+__device__ __forceinline__ float dot4(float4 a, float4 b) {
+  return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
+}
+
+// acc[0] = sum w |x - xm|^2 (or sum w |x|^2 without xm), acc[1 + j] = sum w x . Y_j
+template <int KMAX>
+__global__ void __launch_bounds__(kRedThreads) k_dots(const float4* __restrict__ x,
+                                                      const float4* __restrict__ xm,
+                                                      const float4* __restrict__ Y, long long ys4,
+                                                      int K, long long n4, double* partials,
+                                                      int nblk) {
+  float acc[KMAX + 1];
+#pragma unroll
+  for (int j = 0; j <= KMAX; ++j) acc[j] = 0.f;
+  const long long total = 6 * n4;
+  const long long base = (long long)blockIdx.x * kRedThreads * kPerThread + threadIdx.x;
+#pragma unroll 1
+  for (int r = 0; r < kPerThread; ++r) {
+    const long long q = base + (long long)r * kRedThreads;
+    if (q >= total) break;
+    const float w = (q >= 3 * n4) ? 2.f : 1.f;
+    const float4 a = x[q];
+    float4 d = a;
+    if (xm) {
+      const float4 b = xm[q];
+      d = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+    }
+    acc[0] = fmaf(w, dot4(d, d), acc[0]);
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) {
+      if (j < K) acc[1 + j] = fmaf(w, dot4(a, Y[j * ys4 + q]), acc[1 + j]);
+    }
+  }
+  block_store<KMAX + 1>(acc, K + 1, partials, nblk);
+}
+
+int dots_blocks_for(long long n) {
+  const long long total = 6 * (n / 4);
+  return (int)((total + (long long)kRedThreads * kPerThread - 1) / ((long long)kRedThreads * kPerThread));
+}
+
+cudaError_t launch_dots(const float* x, const float* x_minus, const float* Y, long long ystride,
+                        int K, long long n, double* partials, int nblk, cudaStream_t st) {
+  const long long n4 = n / 4;
+  const float4* x4 = reinterpret_cast<const float4*>(x);
+  const float4* m4 = reinterpret_cast<const float4*>(x_minus);
+  const float4* y4 = reinterpret_cast<const float4*>(Y);
+  const long long ys4 = ystride / 4;
+  if (K <= 2)
+    k_dots<2><<<nblk, kRedThreads, 0, st>>>(x4, m4, y4, ys4, K, n4, partials, nblk);
+  else if (K <= 8)
+    k_dots<8><<<nblk, kRedThreads, 0, st>>>(x4, m4, y4, ys4, K, n4, partials, nblk);
+  else if (K <= 16)
+    k_dots<16><<<nblk, kRedThreads, 0, st>>>(x4, m4, y4, ys4, K, n4, partials, nblk);
+  else if (K <= 32)
+    k_dots<32><<<nblk, kRedThreads, 0, st>>>(x4, m4, y4, ys4, K, n4, partials, nblk);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+// out[j] = sum_b partials[j * nblk + b], one block per j, fixed order.
+__global__ void __launch_bounds__(kRedThreads) k_reduce(const double* __restrict__ partials, int nblk,
+                                                        double* out) {
+  const int j = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += partials[(size_t)j * nblk + b];
+  __shared__ double red[kRedThreads / 32];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kRedThreads / 32; ++w) t += red[w];
+    out[j] = t;
+  }
+}
+
+cudaError_t launch_reduce_partials(const double* partials, int nblk, int m, double* out,
+                                   cudaStream_t st) {
+  k_reduce<<<m, kRedThreads, 0, st>>>(partials, nblk, out);
+  return cudaGetLastError();
+}
+
+// out = xs * x + sum_j coef[j] * Y_j   (coef in float64 on the device)
+// (out may alias x)
+template <int KMAX>
+__global__ void __launch_bounds__(kRedThreads) k_combine(float4* out, const float4* x, float xs,
+                                                         const float4* __restrict__ Y, long long ys4,
+                                                         int K, const double* __restrict__ coef,
+                                                         float cscale, long long total4) {
+  __shared__ float cf[KMAX > 0 ? KMAX : 1];
+  for (int j = threadIdx.x; j < K; j += blockDim.x) cf[j] = (float)(coef[j] * (double)cscale);
+  __syncthreads();
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total4;
+       q += (long long)gridDim.x * blockDim.x) {
+    float4 a = x ? x[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+    a = make_float4(a.x * xs, a.y * xs, a.z * xs, a.w * xs);
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) {
+      if (j < K) {
+        const float4 y = Y[j * ys4 + q];
+        const float c = cf[j];
+        a.x = fmaf(c, y.x, a.x);
+        a.y = fmaf(c, y.y, a.y);
+        a.z = fmaf(c, y.z, a.z);
+        a.w = fmaf(c, y.w, a.w);
+      }
+    }
+    out[q] = a;
+  }
+}
+
+static int stream_blocks(long long total4) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0, v = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    sms = v;
+  }
+  const long long want = (total4 + kRedThreads - 1) / kRedThreads;
+  const long long cap = (long long)sms * 8;
+  return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+cudaError_t launch_combine(float* out, const float* x, float xscale, const float* Y,
+                           long long ystride, int K, const double* coef, float cscale,
+                           long long n, cudaStream_t st) {
+  const long long total4 = 6 * (n / 4);
+  float4* o4 = reinterpret_cast<float4*>(out);
+  const float4* x4 = reinterpret_cast<const float4*>(x);
+  const float4* y4 = reinterpret_cast<const float4*>(Y);
+  const long long ys4 = ystride / 4;
+  const int blocks = stream_blocks(total4);
+  if (K <= 2)
+    k_combine<2><<<blocks, kRedThreads, 0, st>>>(o4, x4, xscale, y4, ys4, K, coef, cscale, total4);
+  else if (K <= 8)
+    k_combine<8><<<blocks, kRedThreads, 0, st>>>(o4, x4, xscale, y4, ys4, K, coef, cscale, total4);
+  else if (K <= 16)
+    k_combine<16><<<blocks, kRedThreads, 0, st>>>(o4, x4, xscale, y4, ys4, K, coef, cscale, total4);
+  else if (K <= 32)
+    k_combine<32><<<blocks, kRedThreads, 0, st>>>(o4, x4, xscale, y4, ys4, K, coef, cscale, total4);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+// sigma = C(x) : eps (Eq. 2.2), optionally stored, and per-component sums.
+__global__ void __launch_bounds__(kRedThreads) k_stress(const float4* __restrict__ eps,
+                                                        const uchar4* __restrict__ phase,
+                                                        const float2* __restrict__ cmat,
+                                                        float4* __restrict__ sig, long long n4,
+                                                        double* partials, int nblk) {
+  float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const long long base = (long long)blockIdx.x * kRedThreads * kPerThread + threadIdx.x;
+#pragma unroll 1
+  for (int r = 0; r < kPerThread; ++r) {
+    const long long q = base + (long long)r * kRedThreads;
+    if (q >= n4) break;
+    const uchar4 ph = phase[q];
+    const float2 m0 = cmat[ph.x], m1 = cmat[ph.y], m2 = cmat[ph.z], m3 = cmat[ph.w];
+    float4 e[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) e[c] = eps[c * n4 + q];
+    const float4 tr = make_float4(e[0].x + e[1].x + e[2].x, e[0].y + e[1].y + e[2].y,
+                                  e[0].z + e[1].z + e[2].z, e[0].w + e[1].w + e[2].w);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      float4 s = make_float4(2.f * m0.y * e[c].x, 2.f * m1.y * e[c].y, 2.f * m2.y * e[c].z,
+                             2.f * m3.y * e[c].w);
+      if (c < 3) {
+        s.x = fmaf(m0.x, tr.x, s.x);
+        s.y = fmaf(m1.x, tr.y, s.y);
+        s.z = fmaf(m2.x, tr.z, s.z);
+        s.w = fmaf(m3.x, tr.w, s.w);
+      }
+      if (sig) sig[c * n4 + q] = s;
+      acc[c] += (s.x + s.y) + (s.z + s.w);
+    }
+  }
+  block_store<6>(acc, 6, partials, nblk);
+}
+
+int stress_blocks_for(long long n) {
+  const long long n4 = n / 4;
+  return (int)((n4 + (long long)kRedThreads * kPerThread - 1) / ((long long)kRedThreads * kPerThread));
+}
+
+cudaError_t launch_stress(const GridDev& g, const float* eps, float* sig, double* partials, int nblk,
+                          cudaStream_t st) {
+  const long long n4 = g.n / 4;
+  k_stress<<<nblk, kRedThreads, 0, st>>>(reinterpret_cast<const float4*>(eps),
+                                         reinterpret_cast<const uchar4*>(g.phase), g.cmat,
+                                         reinterpret_cast<float4*>(sig), n4, partials, nblk);
+  return cudaGetLastError();
+}
+
+// out = a x + b y (y nullable; out may alias x or y)
+__global__ void __launch_bounds__(kRedThreads) k_axpby(float4* out, float a, const float4* x,
+                                                       float b, const float4* y, long long total4) {
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total4;
+       q += (long long)gridDim.x * blockDim.x) {
+    const float4 u = x[q];
+    float4 r = make_float4(a * u.x, a * u.y, a * u.z, a * u.w);
+    if (y) {
+      const float4 v = y[q];
+      r = make_float4(fmaf(b, v.x, r.x), fmaf(b, v.y, r.y), fmaf(b, v.z, r.z), fmaf(b, v.w, r.w));
+    }
+    out[q] = r;
+  }
+}
+
+cudaError_t launch_axpby(float* out, float a, const float* x, float b, const float* y, long long n,
+                         cudaStream_t st) {
+  const long long total4 = 6 * (n / 4);
+  k_axpby<<<stream_blocks(total4), kRedThreads, 0, st>>>(
+      reinterpret_cast<float4*>(out), a, reinterpret_cast<const float4*>(x), b,
+      reinterpret_cast<const float4*>(y), total4);
+  return cudaGetLastError();
+}
+
+__global__ void k_fill(float4* f, float e0, float e1, float e2, float e3, float e4, float e5,
+                       long long n4) {
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < 6 * n4;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(q / n4);
+    const float v = c == 0 ? e0 : c == 1 ? e1 : c == 2 ? e2 : c == 3 ? e3 : c == 4 ? e4 : e5;
+    f[q] = make_float4(v, v, v, v);
+  }
+}
+
+cudaError_t launch_fill(float* f, const double E[6], long long n, cudaStream_t st) {
+  const long long n4 = n / 4;
+  k_fill<<<stream_blocks(6 * n4), kRedThreads, 0, st>>>(
+      reinterpret_cast<float4*>(f), (float)E[0], (float)E[1], (float)E[2], (float)E[3],
+      (float)E[4], (float)E[5], n4);
+  return cudaGetLastError();
+}
+
+// Newton step on the unstable subspace (Eq. 3.11 with H = Z^T F_u Z):
+// sums[0] = |xi - eps|^2, sums[1 + j] = zeta_j = <Z_j, xi>;  M = (I - H)^-1.
+// z+ = z + M (zeta - z);  c = z+ - zeta (so eps_next = xi + Z c);  z_next = z+
+// (z = Z^T eps of the current iterate; z_next = Z^T eps_next).
+// res_out = sqrt(sums[0]) * inv_norm.
+__global__ void k_newton(const double* __restrict__ sums, int p, const double* __restrict__ M,
+                         const double* __restrict__ z, double* __restrict__ c,
+                         double* __restrict__ znext, double* res_out, double inv_norm) {
+  __shared__ double d[64];
+  const int j = threadIdx.x;
+  if (j < p) d[j] = sums[1 + j] - z[j];
+  __syncthreads();
+  if (j < p) {
+    double zp = z[j];
+    for (int k = 0; k < p; ++k) zp += M[j * p + k] * d[k];
+    c[j] = zp - sums[1 + j];
+    znext[j] = zp;
+  }
+  if (j == 0) res_out[0] = sqrt(fmax(sums[0], 0.0)) * inv_norm;
+}
+
+cudaError_t launch_newton(const double* sums, int p, const double* M, const double* z, double* c,
+                          double* znext, double* res_out, double inv_norm, cudaStream_t st) {
+  if (p > 64) return cudaErrorInvalidValue;
+  k_newton<<<1, 64, 0, st>>>(sums, p, M, z, c, znext, res_out, inv_norm);
+  return cudaGetLastError();
+}
+
+}  // namespace rpm

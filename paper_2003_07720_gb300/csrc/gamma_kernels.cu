@@ -1,0 +1,348 @@
+// The Lippmann-Schwinger map of Section 2 as three fused passes over HBM.
+//
+//   pass A (one block per z-plane and tensor component):
+//       tau = (C(x) - C0) : eps  (Eq. 2.3, isotropic phases), packed as
+//       complex rows z_n = tau_2n + i tau_2n+1, forward FFT along x of
+//       length nx/2, real-to-complex untangling, forward FFT along y;
+//       writes the half spectrum in slot order.
+//   pass B (one block per T consecutive (ky, kx) pencils, all 6 components):
+//       forward FFT along z, eps_hat = -Gamma0_hat(xi) : tau_hat per
+//       frequency (Eq. 2.5) with the zero frequency set to E n_vox, inverse
+//       FFT along z.
+//   pass C (one block per z-plane and component): inverse FFT along y,
+//       complex-to-real tangling, inverse FFT along x of length nx/2, scale.
+//
+// The Green operator of the isotropic reference medium is evaluated on the
+// fly from the unit wave vector n = xi/|xi|:
+//   Gamma0_hat : tau_hat = sym(n (x) w),  w = (v - a n (n.v)) / mu0,
+//   v = tau_hat n,  a = (lam0 + mu0) / (lam0 + 2 mu0),
+// obtained from div(C0 : eps(u) + tau) = 0 in Fourier space.
+#include "fft_smem.cuh"
+#include "rpm_internal.h"
+
+namespace rpm {
+
+constexpr int kThreads = 256;
+
+template <int NX, int NY>
+struct PlaneCfg {
+  static constexpr int NXH = NX / 2;
+  static constexpr int SX = NXH + 1;          // x slots of the half spectrum
+  static constexpr int NYP = NY + 1;          // odd column stride in float2
+  static constexpr int PLANE_F2 = SX * NYP;
+  static constexpr int TAB_F2 = NXH + NY + SX;
+};
+
+// X_k from Z_k = a, Z_{M-k} = b (M = nx/2), w = W_nx^k:
+// X_k = (a + conj b)/2 - (i/2) w (a - conj b)
+__device__ __forceinline__ float2 r2c_post(float2 a, float2 b, float2 w) {
+  const float2 s = make_float2(a.x + b.x, a.y - b.y);
+  const float2 d = make_float2(a.x - b.x, a.y + b.y);
+  const float2 u = cmul(w, d);
+  return make_float2(0.5f * (s.x + u.y), 0.5f * (s.y - u.x));
+}
+
+// 2 Z_k from X_k = a, X_{M-k} = b, w = W_nx^k:
+// 2 Z_k = (a + conj b) + i (a - conj b) conj(w)
+__device__ __forceinline__ float2 c2r_pre(float2 a, float2 b, float2 w) {
+  const float2 s = make_float2(a.x + b.x, a.y - b.y);
+  const float2 d = make_float2(a.x - b.x, a.y + b.y);
+  const float2 u = cmulc(d, w);
+  return make_float2(s.x - u.y, s.y + u.x);
+}
+
+template <int NX, int NY>
+__global__ void __launch_bounds__(kThreads) k_pass_a(GridDev g, const float* __restrict__ in,
+                                                     float2* __restrict__ spec, int mode) {
+  using C = PlaneCfg<NX, NY>;
+  extern __shared__ float2 sm[];
+  float2* P = sm;
+  float2* twx = P + C::PLANE_F2;
+  float2* twy = twx + C::NXH;
+  float2* r2c = twy + NY;
+  float2* dm = r2c + C::SX;
+  const int c = blockIdx.x, z = blockIdx.y;
+  for (int i = threadIdx.x; i < C::NXH; i += blockDim.x) twx[i] = g.tw_x[i];
+  for (int i = threadIdx.x; i < NY; i += blockDim.x) twy[i] = g.tw_y[i];
+  for (int i = threadIdx.x; i < C::SX; i += blockDim.x) r2c[i] = g.r2c_w[i];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) dm[i] = g.dmat[i];   // any uint8 id is in range
+  __syncthreads();
+
+  const size_t n2 = (size_t)g.n / 2;                     // float2 per component
+  const size_t z2 = (size_t)z * NY * C::NXH;             // plane offset in float2
+  const float2* in2 = reinterpret_cast<const float2*>(in);
+  const uchar2* ph2 = reinterpret_cast<const uchar2*>(g.phase) + z2;
+  for (int idx = threadIdx.x; idx < NY * C::NXH; idx += blockDim.x) {
+    const int y = idx / C::NXH, h = idx - y * C::NXH;
+    const size_t v = z2 + idx;
+    float2 t;
+    if (mode == GM_RAW_TAU) {
+      t = in2[c * n2 + v];
+    } else {
+      const uchar2 ph = ph2[idx];
+      const float2 d0 = dm[ph.x], d1 = dm[ph.y];
+      const float2 e = in2[c * n2 + v];
+      t = make_float2(2.f * d0.y * e.x, 2.f * d1.y * e.y);
+      if (c < 3) {
+        const float2 a = in2[v], b = in2[n2 + v], d = in2[2 * n2 + v];
+        t.x = fmaf(d0.x, a.x + b.x + d.x, t.x);
+        t.y = fmaf(d1.x, a.y + b.y + d.y, t.y);
+      }
+    }
+    P[h * C::NYP + y] = t;
+  }
+  __syncthreads();
+  smem_fft<C::NXH, false>(P, NY, 1, C::NYP, twx);
+  for (int t = threadIdx.x; t < NY * (C::NXH / 2 + 1); t += blockDim.x) {
+    const int y = t % NY, k = t / NY;
+    if (k == 0) {
+      const float2 z0 = P[y];
+      P[y] = make_float2(z0.x + z0.y, 0.f);
+      P[C::NXH * C::NYP + y] = make_float2(z0.x - z0.y, 0.f);
+    } else {
+      const int kk = C::NXH - k;
+      const int sk = slot_of<C::NXH>(k), skk = slot_of<C::NXH>(kk);
+      const float2 a = P[sk * C::NYP + y], b = P[skk * C::NYP + y];
+      P[sk * C::NYP + y] = r2c_post(a, b, r2c[k]);
+      if (kk != k) P[skk * C::NYP + y] = r2c_post(b, a, r2c[kk]);
+    }
+  }
+  __syncthreads();
+  smem_fft<NY, false>(P, C::SX, C::NYP, 1, twy);
+  float2* out = spec + ((size_t)c * g.nz + z) * g.plane;
+  for (int idx = threadIdx.x; idx < NY * C::SX; idx += blockDim.x) {
+    const int sy = idx / C::SX, sx = idx - sy * C::SX;
+    out[idx] = P[sx * C::NYP + sy];
+  }
+}
+
+template <int NX, int NY>
+__global__ void __launch_bounds__(kThreads) k_pass_c(GridDev g, const float2* __restrict__ spec,
+                                                     float* __restrict__ outp, float scale) {
+  using C = PlaneCfg<NX, NY>;
+  extern __shared__ float2 sm[];
+  float2* P = sm;
+  float2* twx = P + C::PLANE_F2;
+  float2* twy = twx + C::NXH;
+  float2* r2c = twy + NY;
+  const int c = blockIdx.x, z = blockIdx.y;
+  for (int i = threadIdx.x; i < C::NXH; i += blockDim.x) twx[i] = g.tw_x[i];
+  for (int i = threadIdx.x; i < NY; i += blockDim.x) twy[i] = g.tw_y[i];
+  for (int i = threadIdx.x; i < C::SX; i += blockDim.x) r2c[i] = g.r2c_w[i];
+  const float2* src = spec + ((size_t)c * g.nz + z) * g.plane;
+  for (int idx = threadIdx.x; idx < NY * C::SX; idx += blockDim.x) {
+    const int sy = idx / C::SX, sx = idx - sy * C::SX;
+    P[sx * C::NYP + sy] = src[idx];
+  }
+  __syncthreads();
+  smem_fft<NY, true>(P, C::SX, C::NYP, 1, twy);
+  for (int t = threadIdx.x; t < NY * (C::NXH / 2 + 1); t += blockDim.x) {
+    const int y = t % NY, k = t / NY;
+    if (k == 0) {
+      P[y] = c2r_pre(P[y], P[C::NXH * C::NYP + y], make_float2(1.f, 0.f));
+    } else {
+      const int kk = C::NXH - k;
+      const int sk = slot_of<C::NXH>(k), skk = slot_of<C::NXH>(kk);
+      const float2 a = P[sk * C::NYP + y], b = P[skk * C::NYP + y];
+      P[sk * C::NYP + y] = c2r_pre(a, b, r2c[k]);
+      if (kk != k) P[skk * C::NYP + y] = c2r_pre(b, a, r2c[kk]);
+    }
+  }
+  __syncthreads();
+  smem_fft<C::NXH, true>(P, NY, 1, C::NYP, twx);
+  const size_t n2 = (size_t)g.n / 2;
+  float2* out2 = reinterpret_cast<float2*>(outp) + c * n2 + (size_t)z * NY * C::NXH;
+  for (int idx = threadIdx.x; idx < NY * C::NXH; idx += blockDim.x) {
+    const int y = idx / C::NXH, h = idx - y * C::NXH;
+    out2[idx] = cscale(P[h * C::NYP + y], scale);
+  }
+}
+
+struct GammaArgs {
+  float En[6];       // E * n_vox (zero frequency of the strain in GM_FULL_MAP)
+  float a;           // (lam0 + mu0) / (lam0 + 2 mu0)
+  float inv_mu0;
+};
+
+template <int NZ>
+struct PencilCfg {
+  static constexpr int T = NZ >= 256 ? 4 : (NZ >= 128 ? 8 : (NZ >= 64 ? 16 : 32));
+  static constexpr int NZP = (NZ % 2 == 0) ? NZ + 1 : NZ;
+};
+
+// eps_hat = -Gamma0_hat(n) : tau_hat for one frequency (components 11 22 33 23 13 12)
+__device__ __forceinline__ void green_apply(float2* t, float n1, float n2, float n3, float a,
+                                            float inv_mu0) {
+  float2 v1, v2, v3;
+  v1.x = t[0].x * n1 + t[5].x * n2 + t[4].x * n3;
+  v1.y = t[0].y * n1 + t[5].y * n2 + t[4].y * n3;
+  v2.x = t[5].x * n1 + t[1].x * n2 + t[3].x * n3;
+  v2.y = t[5].y * n1 + t[1].y * n2 + t[3].y * n3;
+  v3.x = t[4].x * n1 + t[3].x * n2 + t[2].x * n3;
+  v3.y = t[4].y * n1 + t[3].y * n2 + t[2].y * n3;
+  const float sx = n1 * v1.x + n2 * v2.x + n3 * v3.x;
+  const float sy = n1 * v1.y + n2 * v2.y + n3 * v3.y;
+  float2 w1, w2, w3;
+  w1.x = (v1.x - a * n1 * sx) * inv_mu0;
+  w1.y = (v1.y - a * n1 * sy) * inv_mu0;
+  w2.x = (v2.x - a * n2 * sx) * inv_mu0;
+  w2.y = (v2.y - a * n2 * sy) * inv_mu0;
+  w3.x = (v3.x - a * n3 * sx) * inv_mu0;
+  w3.y = (v3.y - a * n3 * sy) * inv_mu0;
+  t[0] = make_float2(-n1 * w1.x, -n1 * w1.y);
+  t[1] = make_float2(-n2 * w2.x, -n2 * w2.y);
+  t[2] = make_float2(-n3 * w3.x, -n3 * w3.y);
+  t[3] = make_float2(-0.5f * (n2 * w3.x + n3 * w2.x), -0.5f * (n2 * w3.y + n3 * w2.y));
+  t[4] = make_float2(-0.5f * (n1 * w3.x + n3 * w1.x), -0.5f * (n1 * w3.y + n3 * w1.y));
+  t[5] = make_float2(-0.5f * (n1 * w2.x + n2 * w1.x), -0.5f * (n1 * w2.y + n2 * w1.y));
+}
+
+template <int NZ>
+__global__ void __launch_bounds__(kThreads) k_pass_b(GridDev g, float2* __restrict__ spec, int mode,
+                                                     GammaArgs ga) {
+  using C = PencilCfg<NZ>;
+  constexpr int T = C::T, NZP = C::NZP;
+  extern __shared__ float2 sm[];
+  float2* B = sm;
+  float2* twz = B + 6 * T * NZP;
+  for (int i = threadIdx.x; i < NZ; i += blockDim.x) twz[i] = g.tw_z[i];
+  const int m0 = blockIdx.x * T;
+  const int plane = g.plane;
+  for (int idx = threadIdx.x; idx < 6 * NZ * T; idx += blockDim.x) {
+    const int t = idx % T, r = idx / T, z = r % NZ, c = r / NZ;
+    const int m = m0 + t;
+    B[(c * T + t) * NZP + z] =
+        m < plane ? spec[((size_t)c * NZ + z) * plane + m] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  smem_fft<NZ, false>(B, 6 * T, NZP, 1, twz);
+  const int sxn = g.nxh + 1;
+  for (int idx = threadIdx.x; idx < T * NZ; idx += blockDim.x) {
+    const int sz = idx % NZ, t = idx / NZ;
+    const int m = m0 + t;
+    if (m >= plane) continue;
+    const int sy = m / sxn, sx = m - sy * sxn;
+    const int2 fx = g.fx[sx], fy = g.fy[sy];
+    const int kz = freq_of<NZ>(sz);
+    int mz = (2 * kz < NZ) ? kz : kz - NZ;
+    const bool nyqz = (NZ % 2 == 0) && NZ > 1 && (2 * kz == NZ);
+    float2 tv[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) tv[c] = B[(c * T + t) * NZP + sz];
+    const int nnz = (fx.x != 0) + (fy.x != 0) + (mz != 0);
+    if (nnz == 0) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c)
+        tv[c] = make_float2(mode == GM_FULL_MAP ? ga.En[c] : 0.f, 0.f);
+    } else if (g.nyquist == 0 && nnz >= 2 && (fx.y || fy.y || nyqz)) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) tv[c] = make_float2(0.f, 0.f);
+    } else {
+      const float x1 = fx.x * g.inv_lx, x2 = fy.x * g.inv_ly, x3 = mz * g.inv_lz;
+      const float inv = 1.f / sqrtf(x1 * x1 + x2 * x2 + x3 * x3);
+      green_apply(tv, x1 * inv, x2 * inv, x3 * inv, ga.a, ga.inv_mu0);
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) B[(c * T + t) * NZP + sz] = tv[c];
+  }
+  __syncthreads();
+  smem_fft<NZ, true>(B, 6 * T, NZP, 1, twz);
+  for (int idx = threadIdx.x; idx < 6 * NZ * T; idx += blockDim.x) {
+    const int t = idx % T, r = idx / T, z = r % NZ, c = r / NZ;
+    const int m = m0 + t;
+    if (m < plane) spec[((size_t)c * NZ + z) * plane + m] = B[(c * T + t) * NZP + z];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int NX>
+static cudaError_t launch_plane_passes(const GridDev& g, const float* in, float* out,
+                                       float2* spec, int mode, int which, cudaStream_t st) {
+  using C = PlaneCfg<NX, NX>;
+  const dim3 grid(6, g.nz);
+  if (which == 0) {
+    const size_t smem = (size_t)(C::PLANE_F2 + C::TAB_F2 + 256) * sizeof(float2);
+    cudaError_t e = set_smem(k_pass_a<NX, NX>, smem);
+    if (e != cudaSuccess) return e;
+    k_pass_a<NX, NX><<<grid, kThreads, smem, st>>>(g, in, spec, mode);
+  } else {
+    const size_t smem = (size_t)(C::PLANE_F2 + C::TAB_F2) * sizeof(float2);
+    cudaError_t e = set_smem(k_pass_c<NX, NX>, smem);
+    if (e != cudaSuccess) return e;
+    k_pass_c<NX, NX><<<grid, kThreads, smem, st>>>(g, spec, out, 1.0f / (float)g.n);
+  }
+  return cudaGetLastError();
+}
+
+template <int NZ>
+static cudaError_t launch_pencil_pass(const GridDev& g, float2* spec, int mode, const GammaArgs& ga,
+                                      cudaStream_t st) {
+  using C = PencilCfg<NZ>;
+  const size_t smem = (size_t)(6 * C::T * C::NZP + NZ) * sizeof(float2);
+  cudaError_t e = set_smem(k_pass_b<NZ>, smem);
+  if (e != cudaSuccess) return e;
+  const int blocks = (g.plane + C::T - 1) / C::T;
+  k_pass_b<NZ><<<blocks, kThreads, smem, st>>>(g, spec, mode, ga);
+  return cudaGetLastError();
+}
+
+static cudaError_t dispatch_plane(const GridDev& g, const float* in, float* out, float2* spec,
+                                  int mode, int which, cudaStream_t st) {
+  switch (g.nx) {
+    case 4: return launch_plane_passes<4>(g, in, out, spec, mode, which, st);
+    case 8: return launch_plane_passes<8>(g, in, out, spec, mode, which, st);
+    case 16: return launch_plane_passes<16>(g, in, out, spec, mode, which, st);
+    case 32: return launch_plane_passes<32>(g, in, out, spec, mode, which, st);
+    case 64: return launch_plane_passes<64>(g, in, out, spec, mode, which, st);
+    case 128: return launch_plane_passes<128>(g, in, out, spec, mode, which, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+static cudaError_t dispatch_pencil(const GridDev& g, float2* spec, int mode, const GammaArgs& ga,
+                                   cudaStream_t st) {
+  switch (g.nz) {
+    case 1: return launch_pencil_pass<1>(g, spec, mode, ga, st);
+    case 2: return launch_pencil_pass<2>(g, spec, mode, ga, st);
+    case 4: return launch_pencil_pass<4>(g, spec, mode, ga, st);
+    case 8: return launch_pencil_pass<8>(g, spec, mode, ga, st);
+    case 16: return launch_pencil_pass<16>(g, spec, mode, ga, st);
+    case 32: return launch_pencil_pass<32>(g, spec, mode, ga, st);
+    case 64: return launch_pencil_pass<64>(g, spec, mode, ga, st);
+    case 128: return launch_pencil_pass<128>(g, spec, mode, ga, st);
+    case 256: return launch_pencil_pass<256>(g, spec, mode, ga, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+bool grid_supported(int nx, int ny, int nz) {
+  if (nx != ny) return false;
+  const bool plane_ok = nx == 4 || nx == 8 || nx == 16 || nx == 32 || nx == 64 || nx == 128;
+  const bool z_ok = nz == 1 || nz == 2 || nz == 4 || nz == 8 || nz == 16 || nz == 32 || nz == 64 ||
+                    nz == 128 || nz == 256;
+  return plane_ok && z_ok;
+}
+
+cudaError_t launch_apply_gamma(const GridDev& g, const float* in, float* out, float2* spec,
+                               const double E[6], int mode, cudaStream_t st) {
+  GammaArgs ga;
+  for (int c = 0; c < 6; ++c) ga.En[c] = (float)(E ? E[c] * (double)g.n : 0.0);
+  const double l0 = g.lam0, m0 = g.mu0;
+  ga.a = (float)((l0 + m0) / (l0 + 2.0 * m0));
+  ga.inv_mu0 = (float)(1.0 / m0);
+  cudaError_t e = dispatch_plane(g, in, out, spec, mode, 0, st);
+  if (e != cudaSuccess) return e;
+  e = dispatch_pencil(g, spec, mode, ga, st);
+  if (e != cudaSuccess) return e;
+  return dispatch_plane(g, in, out, spec, mode, 1, st);
+}
+
+}  // namespace rpm

@@ -1,0 +1,694 @@
+// Host side of the C ABI declared in include/rpm.h: the context (device
+// buffers, FFT tables, material tables) and the solver loops of
+// Algorithm 1 (basic scheme) and Algorithm 2 (RPM-FFT).
+//
+// Every field-sized step runs in the CUDA kernels of gamma_kernels.cu and
+// field_kernels.cu; the host only sequences launches, takes the small
+// decisions of Algorithm 2 (convergence, the one-or-two-vector rule of
+// Eq. 3.8) and inverts the p x p matrix I - H in float64.
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fft_smem.cuh"
+#include "rpm.h"
+#include "rpm_internal.h"
+
+using namespace rpm;
+
+namespace {
+
+constexpr int kPCap = 32;             // largest basis the kernels accept
+// layout of the small float64 device array
+constexpr int kSums = 0;              // 1 + 32 reduced sums
+constexpr int kZa = 40;               // reduced coordinates z (two buffers)
+constexpr int kZb = 80;
+constexpr int kC = 120;               // Newton correction c
+constexpr int kRes = 160;             // residual
+constexpr int kM = 192;               // (I - H)^-1, 32 x 32
+constexpr int kSmall = kM + kPCap * kPCap;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+struct rpm_ctx {
+  rpm_grid grid{};
+  rpm_options opt{};
+  int p_cap = 0;
+  cudaStream_t st = nullptr;
+  std::vector<rpm_iso> phases;
+  rpm_iso c0{};
+  GridDev g{};
+  long long n = 0;
+  size_t fsz = 0;                    // floats per field (6 n)
+  char* tables = nullptr;
+  uint8_t* phase = nullptr;
+  float2* spec = nullptr;
+  float* fields = nullptr;           // eps[2], xi[3], D[2]
+  float* Z = nullptr;
+  float* W = nullptr;
+  double* partials = nullptr;
+  int nblk = 0;
+  double* dsmall = nullptr;
+  double* hsmall = nullptr;          // pinned host mirror
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  size_t bytes = 0;
+  std::string err;
+  std::vector<double> H;             // host copy of H = Z^T F_u Z (row-major, p x p)
+  int p = 0;
+  long long launches = 0;            // kernels launched by the current solve
+  // event pairs for opt.profile: (start, stop, category 0 = Gamma0, 1 = projections)
+  std::vector<cudaEvent_t> prof_ev;
+  std::vector<int> prof_cat;
+  size_t prof_used = 0;
+};
+
+namespace {
+
+bool ck(rpm_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return true;
+  c->err = std::string(what) + ": " + cudaGetErrorString(e);
+  return false;
+}
+
+rpm_status fail(rpm_ctx* c, rpm_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+void build_twiddles(int L, std::vector<float2>& out) {
+  const int N1 = split_n1(L), N2 = split_n2(L);
+  for (int n2 = 0; n2 < N2; ++n2)
+    for (int k1 = 0; k1 < N1; ++k1) {
+      const double a = -2.0 * M_PI * (double)n2 * (double)k1 / (double)L;
+      out.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
+    }
+}
+
+bool valid_options(const rpm_options& o) {
+  return o.n_max >= 1 && o.p_max >= 0 && o.p_max <= kPCap && o.max_iters >= 0 && o.tol >= 0 &&
+         o.t_ratio >= 0 && (o.nyquist == RPM_NYQ_ZERO_MIXED || o.nyquist == RPM_NYQ_SIGNED) &&
+         o.diverge_factor > 0;
+}
+
+// Gauss-Jordan inverse with partial pivoting (p <= 32), float64.
+bool invert(int p, const std::vector<double>& A, std::vector<double>& inv) {
+  std::vector<double> a(A);
+  inv.assign((size_t)p * p, 0.0);
+  for (int i = 0; i < p; ++i) inv[(size_t)i * p + i] = 1.0;
+  for (int col = 0; col < p; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < p; ++r)
+      if (std::fabs(a[(size_t)r * p + col]) > std::fabs(a[(size_t)piv * p + col])) piv = r;
+    const double pv = a[(size_t)piv * p + col];
+    if (!(std::fabs(pv) > 1e-300)) return false;
+    if (piv != col)
+      for (int k = 0; k < p; ++k) {
+        std::swap(a[(size_t)piv * p + k], a[(size_t)col * p + k]);
+        std::swap(inv[(size_t)piv * p + k], inv[(size_t)col * p + k]);
+      }
+    const double ip = 1.0 / pv;
+    for (int k = 0; k < p; ++k) {
+      a[(size_t)col * p + k] *= ip;
+      inv[(size_t)col * p + k] *= ip;
+    }
+    for (int r = 0; r < p; ++r) {
+      if (r == col) continue;
+      const double f = a[(size_t)r * p + col];
+      if (f == 0.0) continue;
+      for (int k = 0; k < p; ++k) {
+        a[(size_t)r * p + k] -= f * a[(size_t)col * p + k];
+        inv[(size_t)r * p + k] -= f * inv[(size_t)col * p + k];
+      }
+    }
+  }
+  return true;
+}
+
+void upload_materials(rpm_ctx* c, std::vector<float2>& dm, std::vector<float2>& cm) {
+  dm.clear();
+  cm.clear();
+  for (const auto& ph : c->phases) {
+    dm.push_back(make_float2((float)(ph.lambda - c->c0.lambda), (float)(ph.mu - c->c0.mu)));
+    cm.push_back(make_float2((float)ph.lambda, (float)ph.mu));
+  }
+}
+
+// --- thin wrappers that record the failing step ---------------------------
+struct Ops {
+  rpm_ctx* c;
+  // optional event bracket around a group of launches (opt.profile)
+  size_t mark(int cat) {
+    if (!c->opt.profile) return (size_t)-1;
+    if (c->prof_used * 2 + 2 > c->prof_ev.size()) {
+      cudaEvent_t a, b;
+      if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return (size_t)-1;
+      c->prof_ev.push_back(a);
+      c->prof_ev.push_back(b);
+      c->prof_cat.push_back(cat);
+    }
+    const size_t i = c->prof_used++;
+    c->prof_cat[i] = cat;
+    cudaEventRecord(c->prof_ev[2 * i], c->st);
+    return i;
+  }
+  void done(size_t i) {
+    if (i != (size_t)-1) cudaEventRecord(c->prof_ev[2 * i + 1], c->st);
+  }
+  bool gamma(const float* in, float* out, const double* E, int mode) {
+    const size_t m = mark(0);
+    c->launches += 3;
+    const bool ok = ck(c, launch_apply_gamma(c->g, in, out, c->spec, E, mode, c->st), "apply_gamma");
+    done(m);
+    return ok;
+  }
+  // sums[0..K] <- dots of x against Y (see launch_dots)
+  bool dots(const float* x, const float* xm, const float* Y, int K, double* sums) {
+    const size_t m = mark(1);
+    c->launches += 2;
+    bool ok = ck(c, launch_dots(x, xm, Y, (long long)c->fsz, K, c->n, c->partials, c->nblk, c->st),
+                 "dots") &&
+              ck(c, launch_reduce_partials(c->partials, c->nblk, K + 1, sums, c->st), "reduce");
+    done(m);
+    return ok;
+  }
+  bool combine(float* out, const float* x, float xs, const float* Y, int K, const double* coef,
+               float cscale) {
+    const size_t m = mark(1);
+    c->launches += 1;
+    const bool ok =
+        ck(c, launch_combine(out, x, xs, Y, (long long)c->fsz, K, coef, cscale, c->n, c->st),
+           "combine");
+    done(m);
+    return ok;
+  }
+  bool read_small(int off, int count) {
+    if (!ck(c, cudaMemcpyAsync(c->hsmall + off, c->dsmall + off, sizeof(double) * count,
+                               cudaMemcpyDeviceToHost, c->st),
+            "read"))
+      return false;
+    return ck(c, cudaStreamSynchronize(c->st), "sync");
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+void rpm_default_options(rpm_options* o) {
+  if (!o) return;
+  o->n_max = 10;
+  o->p_max = 20;
+  o->max_iters = 5000;
+  o->tol = 1e-6;
+  o->t_ratio = 0.1;
+  o->nyquist = RPM_NYQ_ZERO_MIXED;
+  o->diverge_factor = 1e10;
+  o->max_device_gb = 0.0;
+  o->profile = 0;
+}
+
+int rpm_grid_supported(int nx, int ny, int nz) { return grid_supported(nx, ny, nz) ? 1 : 0; }
+
+const char* rpm_status_string(rpm_status s) {
+  switch (s) {
+    case RPM_OK: return "RPM_OK";
+    case RPM_ERR_INVALID_ARG: return "RPM_ERR_INVALID_ARG";
+    case RPM_ERR_UNSUPPORTED_GRID: return "RPM_ERR_UNSUPPORTED_GRID";
+    case RPM_ERR_OOM: return "RPM_ERR_OOM";
+    case RPM_ERR_CUDA: return "RPM_ERR_CUDA";
+    case RPM_ERR_NOT_CONVERGED: return "RPM_ERR_NOT_CONVERGED";
+    case RPM_ERR_DIVERGED: return "RPM_ERR_DIVERGED";
+    case RPM_ERR_TIMEOUT: return "RPM_ERR_TIMEOUT";
+  }
+  return "RPM_ERR_UNKNOWN";
+}
+
+const char* rpm_last_error(const rpm_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+size_t rpm_device_bytes(const rpm_ctx* c) { return c ? c->bytes : 0; }
+
+void rpm_destroy(rpm_ctx* c) {
+  if (!c) return;
+  cudaFree(c->tables);
+  cudaFree(c->phase);
+  cudaFree(c->spec);
+  cudaFree(c->fields);
+  cudaFree(c->Z);
+  cudaFree(c->W);
+  cudaFree(c->partials);
+  cudaFree(c->dsmall);
+  if (c->hsmall) cudaFreeHost(c->hsmall);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+  delete c;
+}
+
+rpm_status rpm_set_phase(rpm_ctx* c, const uint8_t* phase, int on_device) {
+  if (!c || !phase) return fail(c, RPM_ERR_INVALID_ARG, "null argument");
+  if (!on_device) {
+    for (long long i = 0; i < c->n; ++i)
+      if (phase[i] >= c->phases.size())
+        return fail(c, RPM_ERR_INVALID_ARG, "phase id out of range");
+  }
+  if (!ck(c, cudaMemcpyAsync(c->phase, phase, (size_t)c->n,
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st),
+          "phase upload"))
+    return RPM_ERR_CUDA;
+  return RPM_OK;
+}
+
+rpm_status rpm_set_options(rpm_ctx* c, const rpm_options* o) {
+  if (!c || !o) return fail(c, RPM_ERR_INVALID_ARG, "null argument");
+  if (!valid_options(*o) || o->p_max > c->p_cap)
+    return fail(c, RPM_ERR_INVALID_ARG, "invalid options (p_max above the creation value?)");
+  const int nyq_old = c->opt.nyquist;
+  c->opt = *o;
+  c->g.nyquist = o->nyquist;
+  (void)nyq_old;
+  return RPM_OK;
+}
+
+rpm_status rpm_create(const rpm_grid* grid, const uint8_t* phase, int phase_on_device, int n_phases,
+                      const rpm_iso* phases, rpm_iso c0, const rpm_options* opt, void* stream,
+                      rpm_ctx** out) {
+  if (!out) return RPM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!grid || !phase || !phases || n_phases < 1 || n_phases > 256) return RPM_ERR_INVALID_ARG;
+  rpm_options o;
+  rpm_default_options(&o);
+  if (opt) o = *opt;
+  if (!valid_options(o)) return RPM_ERR_INVALID_ARG;
+  if (!(c0.mu > 0) || !(c0.lambda + 2 * c0.mu > 0)) return RPM_ERR_INVALID_ARG;
+  if (!grid_supported(grid->nx, grid->ny, grid->nz)) return RPM_ERR_UNSUPPORTED_GRID;
+
+  rpm_ctx* c = new rpm_ctx();
+  c->grid = *grid;
+  c->opt = o;
+  c->p_cap = o.p_max;
+  c->st = (cudaStream_t)stream;
+  c->phases.assign(phases, phases + n_phases);
+  c->c0 = c0;
+  const int nx = grid->nx, ny = grid->ny, nz = grid->nz, nxh = nx / 2;
+  c->n = (long long)nx * ny * nz;
+  c->fsz = (size_t)6 * c->n;
+  GridDev& g = c->g;
+  g.nx = nx;
+  g.ny = ny;
+  g.nz = nz;
+  g.nxh = nxh;
+  g.n = c->n;
+  g.plane = ny * (nxh + 1);
+  g.n_phases = n_phases;
+  g.lam0 = (float)c0.lambda;
+  g.mu0 = (float)c0.mu;
+  g.inv_lx = (float)(1.0 / (grid->lx > 0 ? grid->lx : 1.0));
+  g.inv_ly = (float)(1.0 / (grid->ly > 0 ? grid->ly : 1.0));
+  g.inv_lz = (float)(1.0 / (grid->lz > 0 ? grid->lz : 1.0));
+  g.nyquist = o.nyquist;
+
+  // host tables
+  std::vector<float2> twx, twy, twz, r2c, dm, cm;
+  build_twiddles(nxh, twx);
+  build_twiddles(ny, twy);
+  build_twiddles(nz, twz);
+  for (int k = 0; k <= nxh; ++k) {
+    const double a = -2.0 * M_PI * (double)k / (double)nx;
+    r2c.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
+  }
+  std::vector<int2> fx, fy;
+  for (int s = 0; s <= nxh; ++s) {
+    const int k = s < nxh ? freq_of_rt(nxh, s) : nxh;
+    const bool nyq = (k == nxh);
+    fx.push_back(make_int2(nyq ? -k : k, nyq ? 1 : 0));
+  }
+  for (int s = 0; s < ny; ++s) {
+    const int k = freq_of_rt(ny, s);
+    const int m = (2 * k < ny) ? k : k - ny;
+    fy.push_back(make_int2(m, (ny % 2 == 0 && ny > 1 && 2 * k == ny) ? 1 : 0));
+  }
+  upload_materials(c, dm, cm);
+
+  // sizes
+  size_t off = 0;
+  const size_t o_twx = off; off = align_up(off + twx.size() * 8, 256);
+  const size_t o_twy = off; off = align_up(off + twy.size() * 8, 256);
+  const size_t o_twz = off; off = align_up(off + twz.size() * 8, 256);
+  const size_t o_r2c = off; off = align_up(off + r2c.size() * 8, 256);
+  const size_t o_fx = off; off = align_up(off + fx.size() * 8, 256);
+  const size_t o_fy = off; off = align_up(off + fy.size() * 8, 256);
+  const size_t o_dm = off; off = align_up(off + 256 * 8, 256);
+  const size_t o_cm = off; off = align_up(off + 256 * 8, 256);
+  const size_t tab_bytes = off;
+  c->nblk = std::max(dots_blocks_for(c->n), stress_blocks_for(c->n));
+  const size_t fbytes = c->fsz * sizeof(float);
+  const size_t spec_bytes = (size_t)6 * nz * g.plane * sizeof(float2);
+  const size_t need = tab_bytes + align_up((size_t)c->n, 256) + spec_bytes + 7 * fbytes +
+                      2 * (size_t)c->p_cap * fbytes + (size_t)(kPCap + 1) * c->nblk * 8 +
+                      kSmall * 8;
+  if (o.max_device_gb > 0 && (double)need > o.max_device_gb * 1e9) {
+    rpm_destroy(c);
+    return RPM_ERR_OOM;
+  }
+  auto alloc = [&](void** p, size_t b) {
+    if (b == 0) b = 256;
+    cudaError_t e = cudaMalloc(p, b);
+    if (e == cudaSuccess) c->bytes += b;
+    return e;
+  };
+  cudaError_t e = cudaSuccess;
+  if ((e = alloc((void**)&c->tables, tab_bytes)) != cudaSuccess ||
+      (e = alloc((void**)&c->phase, align_up((size_t)c->n, 256))) != cudaSuccess ||
+      (e = alloc((void**)&c->spec, spec_bytes)) != cudaSuccess ||
+      (e = alloc((void**)&c->fields, 7 * fbytes)) != cudaSuccess ||
+      (e = alloc((void**)&c->Z, (size_t)c->p_cap * fbytes)) != cudaSuccess ||
+      (e = alloc((void**)&c->W, (size_t)c->p_cap * fbytes)) != cudaSuccess ||
+      (e = alloc((void**)&c->partials, (size_t)(kPCap + 1) * c->nblk * 8)) != cudaSuccess ||
+      (e = alloc((void**)&c->dsmall, kSmall * 8)) != cudaSuccess) {
+    cudaGetLastError();
+    rpm_destroy(c);
+    return e == cudaErrorMemoryAllocation ? RPM_ERR_OOM : RPM_ERR_CUDA;
+  }
+  if (cudaMallocHost((void**)&c->hsmall, kSmall * 8) != cudaSuccess ||
+      cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+    rpm_destroy(c);
+    return RPM_ERR_CUDA;
+  }
+  char* t = c->tables;
+  auto put = [&](size_t o2, const void* src, size_t b) {
+    return cudaMemcpyAsync(t + o2, src, b, cudaMemcpyHostToDevice, c->st);
+  };
+  std::vector<float2> dm256(256, make_float2(0.f, 0.f)), cm256(256, make_float2(0.f, 0.f));
+  for (int i = 0; i < n_phases; ++i) {
+    dm256[i] = dm[i];
+    cm256[i] = cm[i];
+  }
+  if (put(o_twx, twx.data(), twx.size() * 8) != cudaSuccess ||
+      put(o_twy, twy.data(), twy.size() * 8) != cudaSuccess ||
+      put(o_twz, twz.data(), twz.size() * 8) != cudaSuccess ||
+      put(o_r2c, r2c.data(), r2c.size() * 8) != cudaSuccess ||
+      put(o_fx, fx.data(), fx.size() * 8) != cudaSuccess ||
+      put(o_fy, fy.data(), fy.size() * 8) != cudaSuccess ||
+      put(o_dm, dm256.data(), 256 * 8) != cudaSuccess ||
+      put(o_cm, cm256.data(), 256 * 8) != cudaSuccess ||
+      cudaMemsetAsync(c->dsmall, 0, kSmall * 8, c->st) != cudaSuccess ||
+      cudaStreamSynchronize(c->st) != cudaSuccess) {
+    rpm_destroy(c);
+    return RPM_ERR_CUDA;
+  }
+  g.tw_x = (const float2*)(t + o_twx);
+  g.tw_y = (const float2*)(t + o_twy);
+  g.tw_z = (const float2*)(t + o_twz);
+  g.r2c_w = (const float2*)(t + o_r2c);
+  g.fx = (const int2*)(t + o_fx);
+  g.fy = (const int2*)(t + o_fy);
+  g.dmat = (const float2*)(t + o_dm);
+  g.cmat = (const float2*)(t + o_cm);
+  g.phase = c->phase;
+  rpm_status s = rpm_set_phase(c, phase, phase_on_device);
+  if (s == RPM_OK && cudaStreamSynchronize(c->st) != cudaSuccess) s = RPM_ERR_CUDA;
+  if (s != RPM_OK) {
+    rpm_destroy(c);
+    return s;
+  }
+  *out = c;
+  return RPM_OK;
+}
+
+rpm_status rpm_apply_gamma(rpm_ctx* c, const float* in, const double E[6], float* out, int flags) {
+  if (!c || !in || !out) return fail(c, RPM_ERR_INVALID_ARG, "null argument");
+  if (flags < RPM_GAMMA_FULL_MAP || flags > RPM_GAMMA_RAW_TAU)
+    return fail(c, RPM_ERR_INVALID_ARG, "bad flags");
+  if (flags == RPM_GAMMA_FULL_MAP && !E) return fail(c, RPM_ERR_INVALID_ARG, "E required");
+  if (in == out) return fail(c, RPM_ERR_INVALID_ARG, "in and out alias");
+  Ops ops{c};
+  if (!ops.gamma(in, out, E, flags)) return RPM_ERR_CUDA;
+  return RPM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// One solve of Algorithm 2 (Algorithm 1 when p_max = 0).
+rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* eps_out,
+                      float* sig_out, int out_on_host, rpm_solve_info* info) {
+  Ops ops{c};
+  const rpm_options& o = c->opt;
+  const size_t F = c->fsz;
+  float* epsb[2] = {c->fields, c->fields + F};
+  float* xi[3] = {c->fields + 2 * F, c->fields + 3 * F, c->fields + 4 * F};
+  float* D[2] = {c->fields + 5 * F, c->fields + 6 * F};
+  double* ds = c->dsmall;
+  double* hs = c->hsmall;
+  double En2 = 0;
+  for (int k = 0; k < 6; ++k) En2 += (k < 3 ? 1.0 : 2.0) * E[k] * E[k];
+  const double inv_norm = 1.0 / ((En2 > 0 ? std::sqrt(En2) : 1.0) * std::sqrt((double)c->n));
+
+  rpm_solve_info inf{};
+  inf.status = RPM_OK;
+  c->p = 0;
+  c->launches = 0;
+  c->prof_used = 0;
+  c->H.clear();
+  std::vector<double> M;
+  int zcur = kZa, znext = kZb;
+
+  if (!ck(c, cudaEventRecord(c->ev0, c->st), "event")) return RPM_ERR_CUDA;
+  if (!ck(c, cudaMemsetAsync(ds, 0, kSmall * 8, c->st), "memset")) return RPM_ERR_CUDA;
+  float* eps_cur = epsb[0];
+  if (eps0) {
+    if (!ck(c, cudaMemcpyAsync(eps_cur, eps0, F * 4, cudaMemcpyDeviceToDevice, c->st), "eps0"))
+      return RPM_ERR_CUDA;
+  } else if (++c->launches, !ck(c, launch_fill(eps_cur, E, c->n, c->st), "fill")) {
+    return RPM_ERR_CUDA;
+  }
+  int cur = 0, hist = 1, it = 0, nu = 0, nF = 0;
+  if (!ops.gamma(eps_cur, xi[0], E, GM_FULL_MAP)) return RPM_ERR_CUDA;
+  nF = 1;
+
+  // residual, zeta = Z^T xi and the Newton correction for the current pair (eps, xi)
+  auto eval = [&](double& r) -> bool {
+    if (!ops.dots(xi[cur], eps_cur, c->Z, c->p, ds + kSums)) return false;
+    c->launches += 1;
+    if (!ck(c, launch_newton(ds + kSums, c->p, ds + kM, ds + zcur, ds + kC, ds + znext, ds + kRes,
+                             inv_norm, c->st),
+            "newton"))
+      return false;
+    if (!ops.read_small(kRes, 1)) return false;
+    r = hs[kRes];
+    return true;
+  };
+
+  // In(q, Z) of Algorithm 2 with the QR rule of Eq. 3.8.
+  auto grow = [&]() -> bool {
+    const int prev = (cur + 2) % 3, prev2 = (cur + 1) % 3;
+    double* one = ds + kSums;   // scratch sums
+    // D0 = xi^nu - xi^(nu-1), D1 = xi^(nu-1) - xi^(nu-2)
+    if (!ck(c, (++c->launches, launch_axpby)(D[0], 1.f, xi[cur], -1.f, xi[prev], c->n, c->st), "axpby") ||
+        !ck(c, (++c->launches, launch_axpby)(D[1], 1.f, xi[prev], -1.f, xi[prev2], c->n, c->st), "axpby"))
+      return false;
+    // Q-projection (classical Gram-Schmidt, twice)
+    for (int pass = 0; pass < 2 && c->p > 0; ++pass)
+      for (int k = 0; k < 2; ++k) {
+        if (!ops.dots(D[k], nullptr, c->Z, c->p, one)) return false;
+        if (!ops.combine(D[k], D[k], 1.f, c->Z, c->p, one + 1, -1.f)) return false;
+      }
+    // QR of [D0, D1]
+    if (!ops.dots(D[1], nullptr, D[0], 1, ds + kSums)) return false;   // |D1|^2, <D1,D0>
+    if (!ops.read_small(kSums, 2)) return false;
+    const double n11 = hs[kSums], d10 = hs[kSums + 1];
+    if (!ops.dots(D[0], nullptr, nullptr, 0, ds + kSums)) return false;
+    if (!ops.read_small(kSums, 1)) return false;
+    const double T11 = std::sqrt(std::max(hs[kSums], 0.0));
+    if (!(T11 > 0) || !std::isfinite(T11)) return true;
+    const double T12 = d10 / T11;
+    (void)n11;
+    if (!ck(c, (++c->launches, launch_axpby)(D[1], 1.f, D[1], (float)(-T12 / T11), D[0], c->n, c->st), "axpby"))
+      return false;
+    if (!ops.dots(D[1], nullptr, nullptr, 0, ds + kSums)) return false;
+    if (!ops.read_small(kSums, 1)) return false;
+    const double T22 = std::sqrt(std::max(hs[kSums], 0.0));
+    int ncand = 1;
+    double Tn[2] = {T11, T22};
+    if (std::fabs(T22) > o.t_ratio * std::fabs(T11)) ncand = 2;
+    const int p_old = c->p;
+    const int p_lim = std::min(o.p_max, c->p_cap);
+    for (int k = 0; k < ncand && c->p < p_lim; ++k) {
+      float* u = D[k];
+      if (!(Tn[k] > 0)) continue;
+      if (!ck(c, (++c->launches, launch_axpby)(u, (float)(1.0 / Tn[k]), u, 0.f, nullptr, c->n, c->st), "axpby"))
+        return false;
+      for (int pass = 0; pass < 2 && c->p > 0; ++pass) {
+        if (!ops.dots(u, nullptr, c->Z, c->p, one)) return false;
+        if (!ops.combine(u, u, 1.f, c->Z, c->p, one + 1, -1.f)) return false;
+      }
+      if (!ops.dots(u, nullptr, nullptr, 0, ds + kSums)) return false;
+      if (!ops.read_small(kSums, 1)) return false;
+      const double nu_ = std::sqrt(std::max(hs[kSums], 0.0));
+      if (!(nu_ > 1e-10)) continue;
+      float* zp = c->Z + (size_t)c->p * F;
+      if (!ck(c, (++c->launches, launch_axpby)(zp, (float)(1.0 / nu_), u, 0.f, nullptr, c->n, c->st), "axpby"))
+        return false;
+      if (!ops.gamma(zp, c->W + (size_t)c->p * F, nullptr, GM_LINEAR)) return false;
+      ++nF;
+      ++c->p;
+    }
+    const int p = c->p;
+    if (p == p_old) return true;
+    // extend H: H_ij = <Z_i, F_u Z_j>
+    std::vector<double> Hn((size_t)p * p, 0.0);
+    for (int i = 0; i < p_old; ++i)
+      for (int j = 0; j < p_old; ++j) Hn[(size_t)i * p + j] = c->H[(size_t)i * p_old + j];
+    for (int q = p_old; q < p; ++q) {
+      if (!ops.dots(c->W + (size_t)q * F, nullptr, c->Z, p, ds + kSums)) return false;
+      if (!ops.read_small(kSums, p + 1)) return false;
+      for (int i = 0; i < p; ++i) Hn[(size_t)i * p + q] = hs[kSums + 1 + i];
+      if (!ops.dots(c->Z + (size_t)q * F, nullptr, c->W, p, ds + kSums)) return false;
+      if (!ops.read_small(kSums, p + 1)) return false;
+      for (int j = 0; j < p; ++j) Hn[(size_t)q * p + j] = hs[kSums + 1 + j];
+    }
+    c->H = Hn;
+    std::vector<double> A((size_t)p * p);
+    for (int i = 0; i < p; ++i)
+      for (int j = 0; j < p; ++j) A[(size_t)i * p + j] = (i == j ? 1.0 : 0.0) - Hn[(size_t)i * p + j];
+    if (!invert(p, A, M)) {
+      c->err = "I - H is singular";
+      return false;
+    }
+    if (!ck(c, cudaMemcpyAsync(ds + kM, M.data(), sizeof(double) * p * p, cudaMemcpyHostToDevice,
+                               c->st),
+            "upload M"))
+      return false;
+    // reduced coordinates of the current iterate for the new directions
+    if (!ops.dots(eps_cur, nullptr, c->Z + (size_t)p_old * F, p - p_old, ds + kSums)) return false;
+    if (!ck(c, cudaMemcpyAsync(ds + zcur + p_old, ds + kSums + 1, sizeof(double) * (p - p_old),
+                               cudaMemcpyDeviceToDevice, c->st),
+            "z"))
+      return false;
+    return true;
+  };
+
+  double r = 0;
+  if (!eval(r)) return RPM_ERR_CUDA;
+  const double r0 = r;
+  inf.residual0 = r0;
+  rpm_status status = RPM_OK;
+  for (;;) {
+    if (!std::isfinite(r) || r > o.diverge_factor * r0) {
+      status = RPM_ERR_DIVERGED;
+      break;
+    }
+    if (r <= o.tol) break;
+    if (it >= o.max_iters) {
+      status = RPM_ERR_NOT_CONVERGED;
+      break;
+    }
+    float* eps_next;
+    if (c->p == 0) {
+      eps_next = xi[cur];
+    } else {
+      eps_next = (eps_cur == epsb[0]) ? epsb[1] : epsb[0];
+      if (!ops.combine(eps_next, xi[cur], 1.f, c->Z, c->p, ds + kC, 1.f)) return RPM_ERR_CUDA;
+      std::swap(zcur, znext);
+    }
+    const int nxt = (cur + 1) % 3;
+    if (!ops.gamma(eps_next, xi[nxt], E, GM_FULL_MAP)) return RPM_ERR_CUDA;
+    ++nF;
+    ++it;
+    ++nu;
+    cur = nxt;
+    hist = std::min(hist + 1, 3);
+    eps_cur = eps_next;
+    if (!eval(r)) return RPM_ERR_CUDA;
+    if (std::isfinite(r) && r > o.tol && r <= o.diverge_factor * r0 && nu > o.n_max) {
+      if (c->p < std::min(o.p_max, c->p_cap) && hist == 3) {
+        const int p_before = c->p;
+        if (!grow()) return RPM_ERR_CUDA;
+        if (c->p != p_before && !eval(r)) return RPM_ERR_CUDA;
+      }
+      nu = 0;
+    }
+  }
+
+  // outputs: eps, sigma = C : eps, <sigma>
+  const size_t fb = F * sizeof(float);
+  if (eps_out) {
+    if (!ck(c, cudaMemcpyAsync(eps_out, eps_cur, fb,
+                               out_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->st),
+            "eps_out"))
+      return RPM_ERR_CUDA;
+  }
+  float* sig_dev = sig_out ? (out_on_host ? D[0] : sig_out) : nullptr;
+  if (sig_dev == eps_cur) sig_dev = D[1];
+  c->launches += 2;
+  if (!ck(c, launch_stress(c->g, eps_cur, sig_dev, c->partials, c->nblk, c->st), "stress") ||
+      !ck(c, launch_reduce_partials(c->partials, c->nblk, 6, ds + kSums, c->st), "reduce"))
+    return RPM_ERR_CUDA;
+  if (sig_out && out_on_host) {
+    if (!ck(c, cudaMemcpyAsync(sig_out, sig_dev, fb, cudaMemcpyDeviceToHost, c->st), "sig_out"))
+      return RPM_ERR_CUDA;
+  }
+  if (!ck(c, cudaEventRecord(c->ev1, c->st), "event")) return RPM_ERR_CUDA;
+  if (!ops.read_small(kSums, 6)) return RPM_ERR_CUDA;
+  for (int k = 0; k < 6; ++k) inf.mean_stress[k] = hs[kSums + k] / (double)c->n;
+  float ms = 0;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  inf.ms = ms;
+  for (size_t i = 0; i < c->prof_used; ++i) {
+    float t = 0;
+    if (cudaEventElapsedTime(&t, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]) != cudaSuccess) continue;
+    (c->prof_cat[i] == 0 ? inf.gamma_ms : inf.proj_ms) += t;
+  }
+  inf.launches = c->launches;
+  inf.iters = it;
+  inf.gamma_applies = nF;
+  inf.basis_size = c->p;
+  inf.residual = r;
+  inf.converged = status == RPM_OK;
+  inf.status = status;
+  if (info) *info = inf;
+  if (status == RPM_ERR_NOT_CONVERGED) c->err = "max_iters reached";
+  if (status == RPM_ERR_DIVERGED) c->err = "residual diverged";
+  return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+rpm_status rpm_solve(rpm_ctx* c, const double E[6], const float* eps0, float* eps_out,
+                     float* sig_out, int out_on_host, rpm_solve_info* info) {
+  if (!c || !E) return fail(c, RPM_ERR_INVALID_ARG, "null argument");
+  for (int k = 0; k < 6; ++k)
+    if (!std::isfinite(E[k])) return fail(c, RPM_ERR_INVALID_ARG, "non-finite E");
+  rpm_status s = solve_impl(c, E, eps0, eps_out, sig_out, out_on_host, info);
+  if (s == RPM_ERR_CUDA) {
+    cudaStreamSynchronize(c->st);
+    if (info) info->status = s;
+  }
+  return s;
+}
+
+rpm_status rpm_effective_stiffness(rpm_ctx* c, double C_eff[36], rpm_solve_info info[6]) {
+  if (!c || !C_eff) return fail(c, RPM_ERR_INVALID_ARG, "null argument");
+  rpm_status worst = RPM_OK;
+  for (int j = 0; j < 6; ++j) {
+    double E[6] = {0, 0, 0, 0, 0, 0};
+    E[j] = j < 3 ? 1.0 : 0.5;
+    rpm_solve_info inf{};
+    rpm_status s = rpm_solve(c, E, nullptr, nullptr, nullptr, 0, &inf);
+    if (s == RPM_ERR_CUDA || s == RPM_ERR_INVALID_ARG) return s;
+    if (s != RPM_OK && worst == RPM_OK) worst = s;
+    for (int i = 0; i < 6; ++i) C_eff[i * 6 + j] = inf.mean_stress[i];
+    if (info) info[j] = inf;
+  }
+  return worst;
+}
+
+}  // extern "C"

@@ -1,0 +1,65 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rpm {
+
+// How the zero frequency and the input are treated by one Gamma0 application.
+enum GammaMode {
+  GM_FULL_MAP = 0,   // input eps; output F(eps) = E - Gamma0 * ((C - C0) : eps)
+  GM_LINEAR = 1,     // input eps; output F_u eps = -Gamma0 * ((C - C0) : eps)
+  GM_RAW_TAU = 2,    // input tau; output -Gamma0 * tau (zero mean)
+};
+
+// Device-side description of one grid, its FFT tables and the materials.
+struct GridDev {
+  int nx, ny, nz;        // nx == ny, powers of two
+  int nxh;               // nx / 2
+  long long n;           // voxels
+  int plane;             // ny * (nxh + 1): half-spectrum slots per z-plane
+  // tables (device pointers into one allocation)
+  const float2* tw_x;    // W_{nxh}^(n2*k1), nxh entries
+  const float2* tw_y;    // W_{ny}^(n2*k1), ny entries
+  const float2* tw_z;    // W_{nz}^(n2*k1), nz entries
+  const float2* r2c_w;   // W_{nx}^k, k = 0..nxh
+  const int2* fx;        // per x slot: (signed frequency m, nyquist flag)
+  const int2* fy;        // per y slot
+  const uint8_t* phase;  // [nz][ny][nx]
+  const float2* dmat;    // per phase: (lam - lam0, mu - mu0)
+  const float2* cmat;    // per phase: (lam, mu)
+  int n_phases;
+  float lam0, mu0;
+  float inv_lx, inv_ly, inv_lz;   // 1 / L_j (frequency scaling)
+  int nyquist;           // 0: zero mixed Nyquist frequencies, 1: signed
+};
+
+// One Gamma0 application: in [6][n] -> out [6][n] through the spectrum
+// scratch spec [6][nz][plane] (float2).  E (6 tensor components) is only
+// used in GM_FULL_MAP.  Returns a CUDA error code.
+cudaError_t launch_apply_gamma(const GridDev& g, const float* in, float* out, float2* spec,
+                               const double E[6], int mode, cudaStream_t st);
+
+bool grid_supported(int nx, int ny, int nz);
+
+// ---- field kernels (field_kernels.cu) -------------------------------------
+// Partial sums per block, then one finishing block; see the definitions.
+int dots_blocks_for(long long n);
+int stress_blocks_for(long long n);
+cudaError_t launch_dots(const float* x, const float* x_minus /*nullable*/, const float* Y,
+                        long long ystride, int K, long long n, double* partials, int nblk,
+                        cudaStream_t st);
+cudaError_t launch_reduce_partials(const double* partials, int nblk, int m, double* out,
+                                   cudaStream_t st);
+cudaError_t launch_combine(float* out, const float* x, float xscale, const float* Y,
+                           long long ystride, int K, const double* coef, float cscale,
+                           long long n, cudaStream_t st);
+cudaError_t launch_axpby(float* out, float a, const float* x, float b, const float* y, long long n,
+                         cudaStream_t st);
+cudaError_t launch_stress(const GridDev& g, const float* eps, float* sig /*nullable*/,
+                          double* partials, int nblk, cudaStream_t st);
+cudaError_t launch_fill(float* f, const double E[6], long long n, cudaStream_t st);
+cudaError_t launch_newton(const double* sums, int p, const double* M, const double* z, double* c,
+                          double* znext, double* res_out, double inv_norm, cudaStream_t st);
+
+}  // namespace rpm

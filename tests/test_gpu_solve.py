@@ -1,0 +1,126 @@
+"""Parity of the CUDA solvers (Algorithm 1 and Algorithm 2) with the FP64
+oracle, through the C ABI, plus the error paths."""
+import numpy as np
+import pytest
+
+import microstructure as ms
+from oracle import rpm_oracle as o
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CEFF_TOL = 1e-5     # effective stiffness, relative to max |C_eff|
+FIELD_TOL = 1e-4    # strain field, relative L2
+
+
+@pytest.fixture(scope="module")
+def rpm():
+    from paper_2003_07720_gb300 import rpm as r
+    return r
+
+
+@pytest.fixture(scope="module")
+def sphere32():
+    cell = ms.cell_sphere32(32)
+    prob = o.Problem.from_cell(cell)
+    ref = o.rpm_solve(prob, ms.unit_strain(0), o.Options(tol=1e-11, p_max=20))
+    return cell, prob, ref
+
+
+@pytest.mark.parametrize("p_max", [0, 10])
+def test_sphere32_solve_matches_oracle(rpm, sphere32, p_max):
+    cell, prob, ref = sphere32
+    E = ms.unit_strain(0)
+    eps = torch.empty((6,) + cell.shape, device="cuda")
+    sig = torch.empty_like(eps)
+    with rpm.Context(cell, rpm.rpm_default_options(tol=1e-6, p_max=p_max)) as ctx:
+        st, info = ctx.solve(E, eps_out=eps, sig_out=sig)
+    assert info["converged"] and info["residual"] <= 1e-6
+    if p_max == 0:
+        assert info["basis_size"] == 0
+    else:
+        assert info["basis_size"] > 0
+    e = eps.cpu().numpy().astype(np.float64)
+    err = np.linalg.norm(e - ref.eps) / np.linalg.norm(ref.eps)
+    assert err < FIELD_TOL, err
+    s = sig.cpu().numpy().astype(np.float64)
+    sref = o.stress(prob, ref.eps)
+    assert np.linalg.norm(s - sref) / np.linalg.norm(sref) < FIELD_TOL
+    ms_ = np.array(info["mean_stress"])
+    assert np.max(np.abs(ms_ - ref.mean_stress)) < CEFF_TOL * np.max(np.abs(ref.mean_stress))
+
+
+def test_rpm_iteration_count_tracks_oracle(rpm, sphere32):
+    """Same algorithm at the same tolerance: iteration counts agree closely."""
+    cell, prob, _ = sphere32
+    E = ms.unit_strain(0)
+    r = o.rpm_solve(prob, E, o.Options(tol=1e-6, p_max=10))
+    with rpm.Context(cell, rpm.rpm_default_options(tol=1e-6, p_max=10)) as ctx:
+        st, info = ctx.solve(E)
+    assert abs(info["iters"] - r.iters) <= max(3, r.iters // 5), (info, r.iters)
+
+
+def test_effective_stiffness_sphere16(rpm):
+    cell = ms.cell_sphere32(16)
+    prob = o.Problem.from_cell(cell)
+    C_ref, _ = o.effective_stiffness(prob, o.rpm_solve, o.Options(tol=1e-10, p_max=10))
+    with rpm.Context(cell, rpm.rpm_default_options(tol=1e-6, p_max=10)) as ctx:
+        C, infos, st = ctx.effective_stiffness()
+    assert all(i["converged"] for i in infos)
+    assert np.max(np.abs(C - C_ref)) < CEFF_TOL * np.max(np.abs(C_ref))
+
+
+def test_laminate_closed_form_on_gpu(rpm):
+    """Unequal layers normal to e3, contrast 1e3: exact closed form."""
+    n = 32
+    z = np.arange(n)
+    lay = ((z % 8) < 3).astype(np.uint8)
+    phase = np.broadcast_to(lay[:, None, None], (n, n, n)).copy()
+    l0, m0 = ms.lame(1.0, 0.3)
+    l1, m1 = ms.lame(1e3, 0.3)
+    cell = ms.Cell(phase=phase, lam=np.array([l0, l1]), mu=np.array([m0, m1]),
+                   lam0=0.5 * (l0 + l1), mu0=0.5 * (m0 + m1))
+    ref = o.laminate_ceff([5 / 8, 3 / 8], cell.lam, cell.mu)
+    with rpm.Context(cell, rpm.rpm_default_options(tol=1e-6, p_max=20)) as ctx:
+        C, infos, st = ctx.effective_stiffness()
+    assert np.max(np.abs(C - ref)) < CEFF_TOL * np.max(np.abs(ref))
+
+
+def test_nearvoid_128_solution_is_fixed_point(rpm):
+    """128^3 near-void cell (the benchmark workload): the GPU solution is a
+    fixed point of the oracle's F to the solver tolerance (FP64 check)."""
+    cell = ms.cell_nearvoid(128, 0)
+    prob = o.Problem.from_cell(cell)
+    E = ms.unit_strain(0)
+    eps = torch.empty((6,) + cell.shape, device="cuda")
+    with rpm.Context(cell, rpm.rpm_default_options(tol=1e-6, p_max=20)) as ctx:
+        st, info = ctx.solve(E, eps_out=eps)
+    assert info["converged"]
+    e = eps.cpu().numpy().astype(np.float64)
+    r = o.residual(prob, o.apply_F(prob, e, E), e, E)
+    assert r < 2e-6, r
+    assert np.max(np.abs(e.reshape(6, -1).mean(1) - E)) < 1e-5
+
+
+def test_failure_paths(rpm):
+    cell = ms.cell_sphere32(16)
+    E = ms.unit_strain(0)
+    with rpm.Context(cell, rpm.rpm_default_options(tol=1e-9, p_max=0, max_iters=2)) as ctx:
+        st, info = ctx.solve(E, raise_on_failure=False)
+        assert st == rpm.RPM_ERR_NOT_CONVERGED and info["iters"] == 2
+    # reference medium far below the phases: the basic scheme diverges
+    bad = ms.Cell(phase=cell.phase, lam=cell.lam, mu=cell.mu, lam0=0.05 * cell.lam0,
+                  mu0=0.05 * cell.mu0)
+    with rpm.Context(bad, rpm.rpm_default_options(tol=1e-9, p_max=0, diverge_factor=1e3)) as ctx:
+        st, info = ctx.solve(E, raise_on_failure=False)
+        assert st == rpm.RPM_ERR_DIVERGED
+    # NaN planted in the initial field
+    with rpm.Context(cell) as ctx:
+        eps0 = torch.zeros((6,) + cell.shape, device="cuda")
+        eps0[0, 3, 3, 3] = float("nan")
+        st, info = ctx.solve(E, eps0=eps0, raise_on_failure=False)
+        assert st == rpm.RPM_ERR_DIVERGED
+    # allocation cap injected on the host
+    with pytest.raises(rpm.RpmError) as ei:
+        rpm.Context(cell, rpm.rpm_default_options(max_device_gb=1e-6))
+    assert ei.value.status == rpm.RPM_ERR_OOM
