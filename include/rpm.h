@@ -57,7 +57,11 @@ typedef struct {
   double lambda, mu;
 } rpm_iso;
 
-enum { RPM_NYQ_ZERO_MIXED = 0, RPM_NYQ_SIGNED = 1 };
+/* Frequencies at index N/2 of an even axis (Nyquist) that coexist with another
+ * non-zero frequency component get Gamma0 := 0; pure-axis Nyquist frequencies
+ * are kept.  This keeps Gamma0_hat even in xi, hence the map real-valued.
+ * It is the only mode of this build. */
+enum { RPM_NYQ_ZERO_MIXED = 0 };
 
 typedef struct {
   int n_max;             /* fixed-point steps between basis growths (Alg. 2), default 10 */
@@ -65,7 +69,7 @@ typedef struct {
   int max_iters;         /* fixed-point steps before RPM_ERR_NOT_CONVERGED, default 5000 */
   double tol;            /* stop when |F(eps) - eps| / (|E| sqrt(n)) <= tol, default 1e-6 */
   double t_ratio;        /* kappa: add one vector when |T22| <= kappa |T11| (Eq. 3.8), 0.1 */
-  int nyquist;           /* RPM_NYQ_ZERO_MIXED (default) or RPM_NYQ_SIGNED */
+  int nyquist;           /* RPM_NYQ_ZERO_MIXED (the only accepted value) */
   double diverge_factor; /* RPM_ERR_DIVERGED when residual > factor * initial, 1e10 */
   double max_device_gb;  /* refuse contexts needing more device memory; 0 = no cap */
   int profile;           /* 1: time Gamma0 applications and projections with CUDA events */
@@ -109,6 +113,14 @@ rpm_status rpm_create(const rpm_grid* grid, const uint8_t* phase, int phase_on_d
 
 /* Replace the phase map (same grid); host or device pointer as flagged. */
 rpm_status rpm_set_phase(rpm_ctx* ctx, const uint8_t* phase, int on_device);
+
+/*
+ * Record the residual history of later solves: residuals[k] is the
+ * fixed-point increment residual after k fixed-point steps (k = 0: initial
+ * guess) and basis_sizes[k] the basis size p then, for k < capacity.  Host
+ * arrays owned by the caller; either may be NULL; capacity 0 disables.
+ */
+rpm_status rpm_set_trace(rpm_ctx* ctx, double* residuals, int* basis_sizes, int capacity);
 
 /* Replace the options (p_max may not exceed the value given at creation). */
 rpm_status rpm_set_options(rpm_ctx* ctx, const rpm_options* opt);

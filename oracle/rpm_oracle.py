@@ -56,7 +56,8 @@ PAIRS = ((0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1))
 WEIGHTS = np.array([1.0, 1.0, 1.0, 2.0, 2.0, 2.0])
 
 NYQ_ZERO_MIXED = 0
-NYQ_SIGNED = 1
+NYQ_SIGNED = 1      # plain fftfreq signs everywhere (not used by the tests: the
+                    # result is then not real; see green_mask)
 
 
 # ----------------------------------------------------------------------------

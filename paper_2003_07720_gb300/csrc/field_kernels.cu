@@ -301,7 +301,7 @@ __global__ void k_newton(const double* __restrict__ sums, int p, const double* _
     c[j] = zp - sums[1 + j];
     znext[j] = zp;
   }
-  if (j == 0) res_out[0] = sqrt(fmax(sums[0], 0.0)) * inv_norm;
+  if (j == 0) res_out[0] = sqrt(sums[0]) * inv_norm;   // NaN stays NaN
 }
 
 cudaError_t launch_newton(const double* sums, int p, const double* M, const double* z, double* c,

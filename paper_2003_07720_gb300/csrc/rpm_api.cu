@@ -65,6 +65,10 @@ struct rpm_ctx {
   std::vector<cudaEvent_t> prof_ev;
   std::vector<int> prof_cat;
   size_t prof_used = 0;
+  // optional residual history (host arrays owned by the caller)
+  double* trace_res = nullptr;
+  int* trace_p = nullptr;
+  int trace_cap = 0;
 };
 
 namespace {
@@ -91,8 +95,7 @@ void build_twiddles(int L, std::vector<float2>& out) {
 
 bool valid_options(const rpm_options& o) {
   return o.n_max >= 1 && o.p_max >= 0 && o.p_max <= kPCap && o.max_iters >= 0 && o.tol >= 0 &&
-         o.t_ratio >= 0 && (o.nyquist == RPM_NYQ_ZERO_MIXED || o.nyquist == RPM_NYQ_SIGNED) &&
-         o.diverge_factor > 0;
+         o.t_ratio >= 0 && o.nyquist == RPM_NYQ_ZERO_MIXED && o.diverge_factor > 0;
 }
 
 // Gauss-Jordan inverse with partial pivoting (p <= 32), float64.
@@ -420,6 +423,14 @@ rpm_status rpm_create(const rpm_grid* grid, const uint8_t* phase, int phase_on_d
   return RPM_OK;
 }
 
+rpm_status rpm_set_trace(rpm_ctx* c, double* residuals, int* basis_sizes, int capacity) {
+  if (!c || capacity < 0) return fail(c, RPM_ERR_INVALID_ARG, "bad trace arguments");
+  c->trace_res = residuals;
+  c->trace_p = basis_sizes;
+  c->trace_cap = capacity;
+  return RPM_OK;
+}
+
 rpm_status rpm_apply_gamma(rpm_ctx* c, const float* in, const double E[6], float* out, int flags) {
   if (!c || !in || !out) return fail(c, RPM_ERR_INVALID_ARG, "null argument");
   if (flags < RPM_GAMMA_FULL_MAP || flags > RPM_GAMMA_RAW_TAU)
@@ -574,8 +585,13 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
     return true;
   };
 
+  auto trace = [&](int k, double rr) {
+    if (c->trace_res && k < c->trace_cap) c->trace_res[k] = rr;
+    if (c->trace_p && k < c->trace_cap) c->trace_p[k] = c->p;
+  };
   double r = 0;
   if (!eval(r)) return RPM_ERR_CUDA;
+  trace(0, r);
   const double r0 = r;
   inf.residual0 = r0;
   rpm_status status = RPM_OK;
@@ -606,6 +622,7 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
     hist = std::min(hist + 1, 3);
     eps_cur = eps_next;
     if (!eval(r)) return RPM_ERR_CUDA;
+    trace(it, r);
     if (std::isfinite(r) && r > o.tol && r <= o.diverge_factor * r0 && nu > o.n_max) {
       if (c->p < std::min(o.p_max, c->p_cap) && hist == 3) {
         const int p_before = c->p;

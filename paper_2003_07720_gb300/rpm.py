@@ -26,7 +26,6 @@ RPM_ERR_DIVERGED = 6
 RPM_ERR_TIMEOUT = 7
 
 RPM_NYQ_ZERO_MIXED = 0
-RPM_NYQ_SIGNED = 1
 
 RPM_GAMMA_FULL_MAP = 0
 RPM_GAMMA_LINEAR = 1
@@ -70,7 +69,8 @@ _lib = None
 
 EXPORTS = ("rpm_default_options", "rpm_create", "rpm_set_phase", "rpm_set_options",
            "rpm_apply_gamma", "rpm_solve", "rpm_effective_stiffness", "rpm_last_error",
-           "rpm_status_string", "rpm_device_bytes", "rpm_grid_supported", "rpm_destroy")
+           "rpm_status_string", "rpm_device_bytes", "rpm_grid_supported", "rpm_destroy",
+           "rpm_set_trace")
 
 
 def lib():
@@ -107,6 +107,8 @@ def lib():
     L.rpm_device_bytes.restype = ctypes.c_size_t
     L.rpm_grid_supported.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.rpm_grid_supported.restype = ctypes.c_int
+    L.rpm_set_trace.argtypes = [vp, vp, vp, ctypes.c_int]
+    L.rpm_set_trace.restype = ctypes.c_int
     L.rpm_destroy.argtypes = [vp]
     L.rpm_destroy.restype = None
     _lib = L
@@ -224,6 +226,12 @@ def rpm_effective_stiffness(ctx, raise_on_failure: bool = True):
     return np.array(C[:]).reshape(6, 6), [i.as_dict() for i in infos], st
 
 
+def rpm_set_trace(ctx, residuals, basis_sizes, capacity: int) -> None:
+    """residuals: float64 numpy array, basis_sizes: int32 numpy array (host,
+    kept alive by the caller)."""
+    _check(ctx, lib().rpm_set_trace(ctx, _ptr(residuals), _ptr(basis_sizes), int(capacity)))
+
+
 def rpm_device_bytes(ctx) -> int:
     return int(lib().rpm_device_bytes(ctx))
 
@@ -251,6 +259,12 @@ class Context:
 
     def effective_stiffness(self, **kw):
         return rpm_effective_stiffness(self.handle, **kw)
+
+    def trace(self, capacity: int = 10000):
+        """Start recording residual / basis-size histories; returns the arrays."""
+        self._trace = (np.full(capacity, np.nan), np.full(capacity, -1, dtype=np.int32))
+        rpm_set_trace(self.handle, self._trace[0], self._trace[1], capacity)
+        return self._trace
 
     def close(self):
         if self.handle:

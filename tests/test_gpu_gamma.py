@@ -56,11 +56,6 @@ def test_apply_gamma_matches_oracle(shape, mode):
     assert err < TOL, err
 
 
-def test_apply_gamma_signed_nyquist():
-    got, ref = _run(_cell((8, 8, 8), 5), 0, nyq=1)
-    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < TOL
-
-
 def test_apply_gamma_full_size_128():
     """The 128^3 near-void cell of the benchmark, full map, all elements."""
     cell = ms.cell_nearvoid(128, 0)
