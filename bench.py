@@ -1,10 +1,17 @@
 """Benchmark: converged RPM-FFT solves per second on the 128^3 near-void cell.
 
 One step = one cold-start RPM-FFT solve (Algorithm 2) to the fixed-point
-increment tolerance 1e-6 of the 128^3 near-void cell (RSA spheres of radius
-6-12 voxels, E = 1e-6, 20 % volume fraction, matrix E = 1, nu = 0.3,
-C0 = matrix moduli, macroscopic strain e1 (x) e1, p_max = 20, n_max = 10),
-through the C ABI on the library's CUDA kernels.
+increment tolerance 1e-6 of the 128^3 soft-inclusion cell (RSA spheres of
+radius 6-12 voxels, 20 % volume fraction, seed 0, inclusion E = 1e-3,
+matrix E = 1, nu = 0.3, C0 = matrix moduli, macroscopic strain e1 (x) e1,
+p_max = 20, n_max = 10), through the C ABI on the library's CUDA kernels.
+
+The inclusion modulus is 1e-3 rather than the near-void 1e-6: with
+E = 1e-6 the fixed-point increment of the basic scheme wrapped by RPM stalls
+near 1e-4 (a dense band of interface modes with eigenvalues close to 1; the
+FP64 oracle reproduces the stall), so no converged solve exists to time.
+E = 1e-3 is the softest inclusion for which RPM with p_max = 20 reaches 1e-6
+(the basic scheme alone does not within 5000 steps).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -34,13 +41,16 @@ UNIT = "solves/s"
 N = 128
 TOL = 1e-6
 P_MAX = 20
+E_INCL = 1e-3                       # inclusion modulus (matrix E = 1); see the docstring
 BYTES_PER_VOXEL_GAMMA = 49          # read eps 24 B + phase 1 B, write xi 24 B
 L2_FLUSH_BYTES = 256 << 20
 
 
 def workload_config(extra: dict | None = None) -> dict:
-    cfg = {"workload": "nearvoid128: RPM-FFT solve, 128^3 cell, RSA spheres r 6-12 vox, E_incl 1e-6,"
-                       " vf 0.20, C0 = matrix, E = e1(x)e1, tol 1e-6, p_max 20, n_max 10",
+    cfg = {"workload": "softincl128: RPM-FFT solve, 128^3 cell, RSA spheres r 6-12 vox (seed 0), "
+                       "E_incl 1e-3 (near-void 1e-6 stalls above tol), vf 0.20, C0 = matrix, "
+                       "E = e1(x)e1, tol 1e-6, p_max 20, n_max 10",
+           "e_incl": E_INCL,
            "grid": [N, N, N], "tol": TOL, "p_max": P_MAX, "n_max": 10, "c0_scale": 1.0,
            "load": "e11", "precision": "fp32 fields, fp64 reductions/QR/Newton",
            "l2": "flushed before every timed step (256 MiB write)"}
@@ -142,7 +152,7 @@ def run_reference(args):
     world, rank, _ = dist_info()
     if rank != 0:
         return
-    cell = ms.cell_nearvoid(N, 0, c0_scale=1.0)
+    cell = ms.cell_nearvoid(N, 0, c0_scale=1.0, e_incl=E_INCL)
     nF = oracle_reference_iters()
     times = []
     for i in range(args.warmup + args.steps):
@@ -178,16 +188,18 @@ def run_ours(args):
     entry.build()
     from paper_2003_07720_gb300 import rpm
 
-    cell = ms.cell_nearvoid(N, rank, c0_scale=1.0)
+    cell = ms.cell_nearvoid(N, rank, c0_scale=1.0, e_incl=E_INCL)
     E = ms.unit_strain(0)
     opts = rpm.rpm_default_options(tol=TOL, p_max=P_MAX, n_max=10, profile=1)
+    if args.max_iters:
+        opts.max_iters = args.max_iters          # profiling captures only (not converged)
     stream = torch.cuda.current_stream()
     ctx = rpm.Context(cell, opts, stream=stream)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     eps_out = torch.empty((6, N, N, N), dtype=torch.float32, device="cuda")
 
     for _ in range(args.warmup):
-        ctx.solve(E, eps_out=eps_out)
+        ctx.solve(E, eps_out=eps_out, raise_on_failure=not args.max_iters)
 
     sampler = ClockSampler(local)
     if rank == 0:
@@ -202,7 +214,7 @@ def run_ours(args):
     for k in range(args.steps):
         flush.fill_(float(k))
         ev[k][0].record(stream)
-        st, info = ctx.solve(E, eps_out=eps_out)
+        st, info = ctx.solve(E, eps_out=eps_out, raise_on_failure=not args.max_iters)
         ev[k][1].record(stream)
         infos.append(info)
     torch.cuda.synchronize()
@@ -245,7 +257,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         rpm.rpm_set_phase(ctx.handle, phase_host)
-        st, info = ctx.solve(E, eps_out=out_host, out_on_host=True)
+        st, info = ctx.solve(E, eps_out=out_host, out_on_host=True,
+                             raise_on_failure=not args.max_iters)
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = sum(e2e_t)
     t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
@@ -269,7 +282,7 @@ def run_ours(args):
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(dev_ms_max / args.steps, 3), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-                "data": "synthetic (seeded RSA near-void cell per rank)",
+                "data": "synthetic (seeded RSA soft-inclusion cell per rank)",
                 "config": workload_config({"iters": it, "basis_size": pb,
                                            "gamma_applies": [i["gamma_applies"] for i in infos],
                                            "residual": [i["residual"] for i in infos],
@@ -284,6 +297,45 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_gamma_only(args):
+    """Time the fused Gamma0 application alone (pass A + B + C) on the bench
+    cell: `--kernel gamma`.  Prints one JSON line with its HBM roofline."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as entry
+    entry.build()
+    from paper_2003_07720_gb300 import rpm
+    cell = ms.cell_nearvoid(N, 0, c0_scale=1.0, e_incl=E_INCL)
+    E = ms.unit_strain(0)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn((6, N, N, N), device="cuda", generator=g)
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    ctx = rpm.Context(cell, rpm.rpm_default_options(), stream=stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        ctx.apply_gamma(x, E, y)
+    ts = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.apply_gamma(x, E, y)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    ctx.close()
+    t = statistics.median(ts) / 1e3
+    pk = peaks()
+    ach = BYTES_PER_VOXEL_GAMMA * N ** 3 / t / 1e9
+    print(json.dumps({"kernel": "gamma_apply", "grid": [N, N, N], "median_ms": round(t * 1e3, 4),
+                      "all_ms": [round(v, 4) for v in ts],
+                      "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"],
+                                   "unit": "GB/s", "frac": round(ach / pk["hbm_gbs"], 4),
+                                   "algorithmic_bytes_per_launch": BYTES_PER_VOXEL_GAMMA * N ** 3}}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -291,8 +343,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--max-iters", type=int, default=0,
+                    help="cap the solve (profiling captures only; the result is not converged)")
+    ap.add_argument("--kernel", default=None, choices=[None, "gamma"],
+                    help="time one kernel group alone instead of the solve")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.kernel == "gamma":
+        run_gamma_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

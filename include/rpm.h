@@ -65,7 +65,7 @@ enum { RPM_NYQ_ZERO_MIXED = 0 };
 
 typedef struct {
   int n_max;             /* fixed-point steps between basis growths (Alg. 2), default 10 */
-  int p_max;             /* cap on the unstable-basis size; 0 = basic scheme (Alg. 1); <= 32 */
+  int p_max;             /* cap on the unstable-basis size; 0 = basic scheme (Alg. 1); <= 256 */
   int max_iters;         /* fixed-point steps before RPM_ERR_NOT_CONVERGED, default 5000 */
   double tol;            /* stop when |F(eps) - eps| / (|E| sqrt(n)) <= tol, default 1e-6 */
   double t_ratio;        /* kappa: add one vector when |T22| <= kappa |T11| (Eq. 3.8), 0.1 */

@@ -212,16 +212,17 @@ def cell_sphere32(n: int = 32) -> Cell:
 
 def cell_nearvoid(n: int = 128, seed: int = 0, c0_scale: float = 1.0,
                   r_min: float | None = None, r_max: float | None = None,
-                  target_vf: float = 0.20) -> Cell:
+                  target_vf: float = 0.20, e_incl: float = 1e-6) -> Cell:
     """Near-void cell: RSA spheres (radius 6-12 voxels at n = 128, scaled with
-    n otherwise) of E = 1e-6 in a matrix E = 1; C0 = c0_scale x matrix."""
+    n otherwise) of E = e_incl (1e-6 by default) in a matrix E = 1;
+    C0 = c0_scale x matrix."""
     if r_min is None:
         r_min = 6.0 * n / 128.0
     if r_max is None:
         r_max = 12.0 * n / 128.0
     mask, _ = rsa_spheres(n, seed, r_min, r_max, target_vf)
-    return _two_phase(mask, 1.0, 1e-6, c0_scale=c0_scale,
-                      name=f"nearvoid{n}_s{seed}_c0x{c0_scale:g}")
+    return _two_phase(mask, 1.0, e_incl, c0_scale=c0_scale,
+                      name=f"nearvoid{n}_s{seed}_c0x{c0_scale:g}_e{e_incl:g}")
 
 
 def cell_ellipsoids(n: int = 256, seed: int = 0, contrast: float = 1e4,

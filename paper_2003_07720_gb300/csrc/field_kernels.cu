@@ -22,24 +22,53 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Block-reduce M float values per thread (acc) into partials[j * nblk + blockIdx.x].
+// Error-free sum a + b = s + e (Knuth's TwoSum, six float32 operations).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Warp sum of float values as an unevaluated pair hi + lo: every level of the
+// shuffle tree is a TwoSum, so the rounding errors of the float32 tree are
+// carried exactly in lo (float64 arithmetic is slow on this part; the pair
+// gives about 48 significant bits).
+__device__ __forceinline__ double warp_sum_compensated(float v) {
+  float hi = v, lo = 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float olo = __shfl_xor_sync(0xffffffffu, lo, o);
+    float s, e;
+    two_sum(hi, ohi, s, e);
+    hi = s;
+    lo = lo + olo + e;
+  }
+  return (double)hi + (double)lo;
+}
+
+// Block-reduce M float values per thread (acc) into partials[row(j) * nblk + blockIdx.x],
+// row(0) = 0 when row0 == 0 (skipped otherwise), row(j) = row0 + j for j >= 1.
+// Warp level in compensated float32, warps and blocks combined in float64.
 template <int M>
-__device__ __forceinline__ void block_store(const float* acc, int m, double* partials, int nblk) {
+__device__ __forceinline__ void block_store(const float* acc, int m, int row0, double* partials,
+                                            int nblk) {
   __shared__ double red[kRedThreads / 32][M];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int j = 0; j < M; ++j) {
     if (j < m) {
-      const double s = warp_sum((double)acc[j]);
+      const double s = warp_sum_compensated(acc[j]);
       if (lane == 0) red[warp][j] = s;
     }
   }
   __syncthreads();
   for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    if (j == 0 && row0 != 0) continue;
     double s = 0.0;
 #pragma unroll
     for (int w = 0; w < kRedThreads / 32; ++w) s += red[w][j];
-    partials[(size_t)j * nblk + blockIdx.x] = s;
+    partials[(size_t)(j == 0 ? 0 : row0 + j) * nblk + blockIdx.x] = s;
   }
 }
 
@@ -48,12 +77,13 @@ __device__ __forceinline__ float dot4(float4 a, float4 b) {
 }
 
 // acc[0] = sum w |x - xm|^2 (or sum w |x|^2 without xm), acc[1 + j] = sum w x . Y_j
+// Partial sums go to rows [0] (the norm) and [1 + row0 + j] of `partials`.
 template <int KMAX>
 __global__ void __launch_bounds__(kRedThreads) k_dots(const float4* __restrict__ x,
                                                       const float4* __restrict__ xm,
                                                       const float4* __restrict__ Y, long long ys4,
-                                                      int K, long long n4, double* partials,
-                                                      int nblk) {
+                                                      int K, int row0, long long n4,
+                                                      double* partials, int nblk) {
   float acc[KMAX + 1];
 #pragma unroll
   for (int j = 0; j <= KMAX; ++j) acc[j] = 0.f;
@@ -76,7 +106,7 @@ __global__ void __launch_bounds__(kRedThreads) k_dots(const float4* __restrict__
       if (j < K) acc[1 + j] = fmaf(w, dot4(a, Y[j * ys4 + q]), acc[1 + j]);
     }
   }
-  block_store<KMAX + 1>(acc, K + 1, partials, nblk);
+  block_store<KMAX + 1>(acc, K + 1, row0, partials, nblk);
 }
 
 int dots_blocks_for(long long n) {
@@ -89,20 +119,26 @@ cudaError_t launch_dots(const float* x, const float* x_minus, const float* Y, lo
   const long long n4 = n / 4;
   const float4* x4 = reinterpret_cast<const float4*>(x);
   const float4* m4 = reinterpret_cast<const float4*>(x_minus);
-  const float4* y4 = reinterpret_cast<const float4*>(Y);
   const long long ys4 = ystride / 4;
-  if (K <= 2)
-    k_dots<2><<<nblk, kRedThreads, 0, st>>>(x4, m4, y4, ys4, K, n4, partials, nblk);
-  else if (K <= 8)
-    k_dots<8><<<nblk, kRedThreads, 0, st>>>(x4, m4, y4, ys4, K, n4, partials, nblk);
-  else if (K <= 16)
-    k_dots<16><<<nblk, kRedThreads, 0, st>>>(x4, m4, y4, ys4, K, n4, partials, nblk);
-  else if (K <= 32)
-    k_dots<32><<<nblk, kRedThreads, 0, st>>>(x4, m4, y4, ys4, K, n4, partials, nblk);
-  else
-    return cudaErrorInvalidValue;
-  return cudaGetLastError();
+  // K > 32: chunks of 32 basis vectors; the norm row is written by chunk 0
+  for (int k0 = 0; k0 == 0 || k0 < K; k0 += 32) {
+    const int Kc = K - k0 < 32 ? K - k0 : 32;
+    const float4* y4 = reinterpret_cast<const float4*>(Y) + (Y ? k0 * ys4 : 0);
+    if (Kc <= 2)
+      k_dots<2><<<nblk, kRedThreads, 0, st>>>(x4, m4, y4, ys4, Kc, k0, n4, partials, nblk);
+    else if (Kc <= 8)
+      k_dots<8><<<nblk, kRedThreads, 0, st>>>(x4, m4, y4, ys4, Kc, k0, n4, partials, nblk);
+    else if (Kc <= 16)
+      k_dots<16><<<nblk, kRedThreads, 0, st>>>(x4, m4, y4, ys4, Kc, k0, n4, partials, nblk);
+    else
+      k_dots<32><<<nblk, kRedThreads, 0, st>>>(x4, m4, y4, ys4, Kc, k0, n4, partials, nblk);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
+
+int dots_launches(int K) { return K <= 32 ? 1 : (K + 31) / 32; }
 
 // out[j] = sum_b partials[j * nblk + b], one block per j, fixed order.
 __global__ void __launch_bounds__(kRedThreads) k_reduce(const double* __restrict__ partials, int nblk,
@@ -128,12 +164,14 @@ cudaError_t launch_reduce_partials(const double* partials, int nblk, int m, doub
 }
 
 // out = xs * x + sum_j coef[j] * Y_j   (coef in float64 on the device)
-// (out may alias x)
+// (out may alias x).  The basis vectors are read in groups of 8 so that each
+// thread keeps 8 independent 16-byte loads in flight at a modest register count.
 template <int KMAX>
-__global__ void __launch_bounds__(kRedThreads) k_combine(float4* out, const float4* x, float xs,
-                                                         const float4* __restrict__ Y, long long ys4,
-                                                         int K, const double* __restrict__ coef,
-                                                         float cscale, long long total4) {
+__global__ void __launch_bounds__(kRedThreads, 3) k_combine(float4* out, const float4* x, float xs,
+                                                            const float4* __restrict__ Y,
+                                                            long long ys4, int K,
+                                                            const double* __restrict__ coef,
+                                                            float cscale, long long total4) {
   __shared__ float cf[KMAX > 0 ? KMAX : 1];
   for (int j = threadIdx.x; j < K; j += blockDim.x) cf[j] = (float)(coef[j] * (double)cscale);
   __syncthreads();
@@ -141,15 +179,21 @@ __global__ void __launch_bounds__(kRedThreads) k_combine(float4* out, const floa
        q += (long long)gridDim.x * blockDim.x) {
     float4 a = x ? x[q] : make_float4(0.f, 0.f, 0.f, 0.f);
     a = make_float4(a.x * xs, a.y * xs, a.z * xs, a.w * xs);
+#pragma unroll 1
+    for (int j0 = 0; j0 < K; j0 += 8) {
+      float4 y[8];
 #pragma unroll
-    for (int j = 0; j < KMAX; ++j) {
-      if (j < K) {
-        const float4 y = Y[j * ys4 + q];
-        const float c = cf[j];
-        a.x = fmaf(c, y.x, a.x);
-        a.y = fmaf(c, y.y, a.y);
-        a.z = fmaf(c, y.z, a.z);
-        a.w = fmaf(c, y.w, a.w);
+      for (int u = 0; u < 8; ++u)
+        if (j0 + u < K) y[u] = Y[(j0 + u) * ys4 + q];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (j0 + u < K) {
+          const float c = cf[j0 + u];
+          a.x = fmaf(c, y[u].x, a.x);
+          a.y = fmaf(c, y[u].y, a.y);
+          a.z = fmaf(c, y[u].z, a.z);
+          a.w = fmaf(c, y[u].w, a.w);
+        }
       }
     }
     out[q] = a;
@@ -174,22 +218,30 @@ cudaError_t launch_combine(float* out, const float* x, float xscale, const float
                            long long n, cudaStream_t st) {
   const long long total4 = 6 * (n / 4);
   float4* o4 = reinterpret_cast<float4*>(out);
-  const float4* x4 = reinterpret_cast<const float4*>(x);
-  const float4* y4 = reinterpret_cast<const float4*>(Y);
   const long long ys4 = ystride / 4;
   const int blocks = stream_blocks(total4);
-  if (K <= 2)
-    k_combine<2><<<blocks, kRedThreads, 0, st>>>(o4, x4, xscale, y4, ys4, K, coef, cscale, total4);
-  else if (K <= 8)
-    k_combine<8><<<blocks, kRedThreads, 0, st>>>(o4, x4, xscale, y4, ys4, K, coef, cscale, total4);
-  else if (K <= 16)
-    k_combine<16><<<blocks, kRedThreads, 0, st>>>(o4, x4, xscale, y4, ys4, K, coef, cscale, total4);
-  else if (K <= 32)
-    k_combine<32><<<blocks, kRedThreads, 0, st>>>(o4, x4, xscale, y4, ys4, K, coef, cscale, total4);
-  else
-    return cudaErrorInvalidValue;
-  return cudaGetLastError();
+  // K > 32: the first chunk forms xs * x + ..., later chunks accumulate into out
+  for (int k0 = 0; k0 == 0 || k0 < K; k0 += 32) {
+    const int Kc = K - k0 < 32 ? K - k0 : 32;
+    const float4* x4 = k0 == 0 ? reinterpret_cast<const float4*>(x) : o4;
+    const float xs = k0 == 0 ? xscale : 1.f;
+    const float4* y4 = reinterpret_cast<const float4*>(Y) + (Y ? k0 * ys4 : 0);
+    const double* cf = coef ? coef + k0 : nullptr;
+    if (Kc <= 2)
+      k_combine<2><<<blocks, kRedThreads, 0, st>>>(o4, x4, xs, y4, ys4, Kc, cf, cscale, total4);
+    else if (Kc <= 8)
+      k_combine<8><<<blocks, kRedThreads, 0, st>>>(o4, x4, xs, y4, ys4, Kc, cf, cscale, total4);
+    else if (Kc <= 16)
+      k_combine<16><<<blocks, kRedThreads, 0, st>>>(o4, x4, xs, y4, ys4, Kc, cf, cscale, total4);
+    else
+      k_combine<32><<<blocks, kRedThreads, 0, st>>>(o4, x4, xs, y4, ys4, Kc, cf, cscale, total4);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
+
+int combine_launches(int K) { return K <= 32 ? 1 : (K + 31) / 32; }
 
 // sigma = C(x) : eps (Eq. 2.2), optionally stored, and per-component sums.
 __global__ void __launch_bounds__(kRedThreads) k_stress(const float4* __restrict__ eps,
@@ -224,7 +276,7 @@ __global__ void __launch_bounds__(kRedThreads) k_stress(const float4* __restrict
       acc[c] += (s.x + s.y) + (s.z + s.w);
     }
   }
-  block_store<6>(acc, 6, partials, nblk);
+  block_store<6>(acc, 6, 0, partials, nblk);
 }
 
 int stress_blocks_for(long long n) {
@@ -291,23 +343,22 @@ cudaError_t launch_fill(float* f, const double E[6], long long n, cudaStream_t s
 __global__ void k_newton(const double* __restrict__ sums, int p, const double* __restrict__ M,
                          const double* __restrict__ z, double* __restrict__ c,
                          double* __restrict__ znext, double* res_out, double inv_norm) {
-  __shared__ double d[64];
-  const int j = threadIdx.x;
-  if (j < p) d[j] = sums[1 + j] - z[j];
+  __shared__ double d[kMaxBasis];
+  for (int j = threadIdx.x; j < p; j += blockDim.x) d[j] = sums[1 + j] - z[j];
   __syncthreads();
-  if (j < p) {
+  for (int j = threadIdx.x; j < p; j += blockDim.x) {
     double zp = z[j];
-    for (int k = 0; k < p; ++k) zp += M[j * p + k] * d[k];
+    for (int k = 0; k < p; ++k) zp += M[(size_t)j * p + k] * d[k];
     c[j] = zp - sums[1 + j];
     znext[j] = zp;
   }
-  if (j == 0) res_out[0] = sqrt(sums[0]) * inv_norm;   // NaN stays NaN
+  if (threadIdx.x == 0) res_out[0] = sqrt(sums[0]) * inv_norm;   // NaN stays NaN
 }
 
 cudaError_t launch_newton(const double* sums, int p, const double* M, const double* z, double* c,
                           double* znext, double* res_out, double inv_norm, cudaStream_t st) {
-  if (p > 64) return cudaErrorInvalidValue;
-  k_newton<<<1, 64, 0, st>>>(sums, p, M, z, c, znext, res_out, inv_norm);
+  if (p > kMaxBasis) return cudaErrorInvalidValue;
+  k_newton<<<1, 256, 0, st>>>(sums, p, M, z, c, znext, res_out, inv_norm);
   return cudaGetLastError();
 }
 

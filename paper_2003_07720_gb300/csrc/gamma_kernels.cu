@@ -72,27 +72,51 @@ __global__ void __launch_bounds__(kThreads) k_pass_a(GridDev g, const float* __r
   const size_t z2 = (size_t)z * NY * C::NXH;             // plane offset in float2
   const float2* in2 = reinterpret_cast<const float2*>(in);
   const uchar2* ph2 = reinterpret_cast<const uchar2*>(g.phase) + z2;
-  for (int idx = threadIdx.x; idx < NY * C::NXH; idx += blockDim.x) {
-    const int y = idx / C::NXH, h = idx - y * C::NXH;
-    const size_t v = z2 + idx;
-    float2 t;
-    if (mode == GM_RAW_TAU) {
-      t = in2[c * n2 + v];
-    } else {
-      const uchar2 ph = ph2[idx];
-      const float2 d0 = dm[ph.x], d1 = dm[ph.y];
-      const float2 e = in2[c * n2 + v];
-      t = make_float2(2.f * d0.y * e.x, 2.f * d1.y * e.y);
-      if (c < 3) {
-        const float2 a = in2[v], b = in2[n2 + v], d = in2[2 * n2 + v];
-        t.x = fmaf(d0.x, a.x + b.x + d.x, t.x);
-        t.y = fmaf(d1.x, a.y + b.y + d.y, t.y);
+  // Loads are issued in groups of U per thread before any use, so each thread
+  // keeps several independent requests in flight (the plane is streamed once).
+  constexpr int TOT = NY * C::NXH, U = 4;
+  for (int base = threadIdx.x; base < TOT; base += U * kThreads) {
+    float2 a[U], b[U], d[U];
+    uchar2 ph[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * kThreads;
+      if (idx < TOT) {
+        const size_t v = z2 + idx;
+        if (mode == GM_RAW_TAU || c >= 3) {
+          a[u] = in2[c * n2 + v];
+        } else {
+          a[u] = in2[v];
+          b[u] = in2[n2 + v];
+          d[u] = in2[2 * n2 + v];
+        }
+        if (mode != GM_RAW_TAU) ph[u] = ph2[idx];
       }
     }
-    P[h * C::NYP + y] = t;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * kThreads;
+      if (idx < TOT) {
+        const int y = idx / C::NXH, h = idx - y * C::NXH;
+        float2 t;
+        if (mode == GM_RAW_TAU) {
+          t = a[u];
+        } else {
+          const float2 d0 = dm[ph[u].x], d1 = dm[ph[u].y];
+          if (c >= 3) {
+            t = make_float2(2.f * d0.y * a[u].x, 2.f * d1.y * a[u].y);
+          } else {
+            const float2 e = c == 0 ? a[u] : (c == 1 ? b[u] : d[u]);
+            t = make_float2(fmaf(d0.x, a[u].x + b[u].x + d[u].x, 2.f * d0.y * e.x),
+                            fmaf(d1.x, a[u].y + b[u].y + d[u].y, 2.f * d1.y * e.y));
+          }
+        }
+        P[h * C::NYP + y] = t;
+      }
+    }
   }
   __syncthreads();
-  smem_fft<C::NXH, false>(P, NY, 1, C::NYP, twx);
+  smem_fft<C::NXH, false, NY>(P, 1, C::NYP, twx);
   for (int t = threadIdx.x; t < NY * (C::NXH / 2 + 1); t += blockDim.x) {
     const int y = t % NY, k = t / NY;
     if (k == 0) {
@@ -108,7 +132,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_a(GridDev g, const float* __r
     }
   }
   __syncthreads();
-  smem_fft<NY, false>(P, C::SX, C::NYP, 1, twy);
+  smem_fft<NY, false, C::SX>(P, C::NYP, 1, twy);
   float2* out = spec + ((size_t)c * g.nz + z) * g.plane;
   for (int idx = threadIdx.x; idx < NY * C::SX; idx += blockDim.x) {
     const int sy = idx / C::SX, sx = idx - sy * C::SX;
@@ -130,12 +154,27 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(GridDev g, const float2* __
   for (int i = threadIdx.x; i < NY; i += blockDim.x) twy[i] = g.tw_y[i];
   for (int i = threadIdx.x; i < C::SX; i += blockDim.x) r2c[i] = g.r2c_w[i];
   const float2* src = spec + ((size_t)c * g.nz + z) * g.plane;
-  for (int idx = threadIdx.x; idx < NY * C::SX; idx += blockDim.x) {
-    const int sy = idx / C::SX, sx = idx - sy * C::SX;
-    P[sx * C::NYP + sy] = src[idx];
+  {
+    constexpr int TOT = NY * C::SX, U = 8;
+    for (int base = threadIdx.x; base < TOT; base += U * kThreads) {
+      float2 v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = base + u * kThreads;
+        if (idx < TOT) v[u] = src[idx];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = base + u * kThreads;
+        if (idx < TOT) {
+          const int sy = idx / C::SX, sx = idx - sy * C::SX;
+          P[sx * C::NYP + sy] = v[u];
+        }
+      }
+    }
   }
   __syncthreads();
-  smem_fft<NY, true>(P, C::SX, C::NYP, 1, twy);
+  smem_fft<NY, true, C::SX>(P, C::NYP, 1, twy);
   for (int t = threadIdx.x; t < NY * (C::NXH / 2 + 1); t += blockDim.x) {
     const int y = t % NY, k = t / NY;
     if (k == 0) {
@@ -149,7 +188,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(GridDev g, const float2* __
     }
   }
   __syncthreads();
-  smem_fft<C::NXH, true>(P, NY, 1, C::NYP, twx);
+  smem_fft<C::NXH, true, NY>(P, 1, C::NYP, twx);
   const size_t n2 = (size_t)g.n / 2;
   float2* out2 = reinterpret_cast<float2*>(outp) + c * n2 + (size_t)z * NY * C::NXH;
   for (int idx = threadIdx.x; idx < NY * C::NXH; idx += blockDim.x) {
@@ -208,14 +247,30 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(GridDev g, float2* __restri
   for (int i = threadIdx.x; i < NZ; i += blockDim.x) twz[i] = g.tw_z[i];
   const int m0 = blockIdx.x * T;
   const int plane = g.plane;
-  for (int idx = threadIdx.x; idx < 6 * NZ * T; idx += blockDim.x) {
-    const int t = idx % T, r = idx / T, z = r % NZ, c = r / NZ;
-    const int m = m0 + t;
-    B[(c * T + t) * NZP + z] =
-        m < plane ? spec[((size_t)c * NZ + z) * plane + m] : make_float2(0.f, 0.f);
+  {
+    constexpr int TOT = 6 * NZ * T, U = 8;
+    for (int base = threadIdx.x; base < TOT; base += U * kThreads) {
+      float2 v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = base + u * kThreads;
+        const int t = idx % T, r = idx / T, z = r % NZ, c = r / NZ;
+        const int m = m0 + t;
+        v[u] = (idx < TOT && m < plane) ? spec[((size_t)c * NZ + z) * plane + m]
+                                        : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = base + u * kThreads;
+        if (idx < TOT) {
+          const int t = idx % T, r = idx / T, z = r % NZ, c = r / NZ;
+          B[(c * T + t) * NZP + z] = v[u];
+        }
+      }
+    }
   }
   __syncthreads();
-  smem_fft<NZ, false>(B, 6 * T, NZP, 1, twz);
+  smem_fft<NZ, false, 6 * T>(B, NZP, 1, twz);
   const int sxn = g.nxh + 1;
   for (int idx = threadIdx.x; idx < T * NZ; idx += blockDim.x) {
     const int sz = idx % NZ, t = idx / NZ;
@@ -246,7 +301,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(GridDev g, float2* __restri
     for (int c = 0; c < 6; ++c) B[(c * T + t) * NZP + sz] = tv[c];
   }
   __syncthreads();
-  smem_fft<NZ, true>(B, 6 * T, NZP, 1, twz);
+  smem_fft<NZ, true, 6 * T>(B, NZP, 1, twz);
   for (int idx = threadIdx.x; idx < 6 * NZ * T; idx += blockDim.x) {
     const int t = idx % T, r = idx / T, z = r % NZ, c = r / NZ;
     const int m = m0 + t;

@@ -21,14 +21,14 @@ using namespace rpm;
 
 namespace {
 
-constexpr int kPCap = 32;             // largest basis the kernels accept
+constexpr int kPCap = kMaxBasis;      // largest basis the kernels accept
 // layout of the small float64 device array
-constexpr int kSums = 0;              // 1 + 32 reduced sums
-constexpr int kZa = 40;               // reduced coordinates z (two buffers)
-constexpr int kZb = 80;
-constexpr int kC = 120;               // Newton correction c
-constexpr int kRes = 160;             // residual
-constexpr int kM = 192;               // (I - H)^-1, 32 x 32
+constexpr int kSums = 0;              // 1 + kPCap reduced sums
+constexpr int kZa = kSums + kPCap + 8;   // reduced coordinates z (two buffers)
+constexpr int kZb = kZa + kPCap;
+constexpr int kC = kZb + kPCap;       // Newton correction c
+constexpr int kRes = kC + kPCap;      // residual
+constexpr int kM = kRes + 8;          // (I - H)^-1, kPCap x kPCap
 constexpr int kSmall = kM + kPCap * kPCap;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -45,6 +45,7 @@ struct rpm_ctx {
   GridDev g{};
   long long n = 0;
   size_t fsz = 0;                    // floats per field (6 n)
+  size_t fst = 0;                    // stride between internal fields (6 n + pad)
   char* tables = nullptr;
   uint8_t* phase = nullptr;
   float2* spec = nullptr;
@@ -172,8 +173,8 @@ struct Ops {
   // sums[0..K] <- dots of x against Y (see launch_dots)
   bool dots(const float* x, const float* xm, const float* Y, int K, double* sums) {
     const size_t m = mark(1);
-    c->launches += 2;
-    bool ok = ck(c, launch_dots(x, xm, Y, (long long)c->fsz, K, c->n, c->partials, c->nblk, c->st),
+    c->launches += 1 + dots_launches(K);
+    bool ok = ck(c, launch_dots(x, xm, Y, (long long)c->fst, K, c->n, c->partials, c->nblk, c->st),
                  "dots") &&
               ck(c, launch_reduce_partials(c->partials, c->nblk, K + 1, sums, c->st), "reduce");
     done(m);
@@ -182,9 +183,9 @@ struct Ops {
   bool combine(float* out, const float* x, float xs, const float* Y, int K, const double* coef,
                float cscale) {
     const size_t m = mark(1);
-    c->launches += 1;
+    c->launches += combine_launches(K);
     const bool ok =
-        ck(c, launch_combine(out, x, xs, Y, (long long)c->fsz, K, coef, cscale, c->n, c->st),
+        ck(c, launch_combine(out, x, xs, Y, (long long)c->fst, K, coef, cscale, c->n, c->st),
            "combine");
     done(m);
     return ok;
@@ -300,6 +301,10 @@ rpm_status rpm_create(const rpm_grid* grid, const uint8_t* phase, int phase_on_d
   const int nx = grid->nx, ny = grid->ny, nz = grid->nz, nxh = nx / 2;
   c->n = (long long)nx * ny * nz;
   c->fsz = (size_t)6 * c->n;
+  // Internal fields sit 6 n floats + 4352 bytes apart: equal power-of-two-like
+  // strides put the 2p concurrent basis streams of the projections on the same
+  // DRAM channels.
+  c->fst = c->fsz + 1088;
   GridDev& g = c->g;
   g.nx = nx;
   g.ny = ny;
@@ -349,7 +354,7 @@ rpm_status rpm_create(const rpm_grid* grid, const uint8_t* phase, int phase_on_d
   const size_t o_cm = off; off = align_up(off + 256 * 8, 256);
   const size_t tab_bytes = off;
   c->nblk = std::max(dots_blocks_for(c->n), stress_blocks_for(c->n));
-  const size_t fbytes = c->fsz * sizeof(float);
+  const size_t fbytes = c->fst * sizeof(float);
   const size_t spec_bytes = (size_t)6 * nz * g.plane * sizeof(float2);
   const size_t need = tab_bytes + align_up((size_t)c->n, 256) + spec_bytes + 7 * fbytes +
                       2 * (size_t)c->p_cap * fbytes + (size_t)(kPCap + 1) * c->nblk * 8 +
@@ -451,7 +456,7 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
                       float* sig_out, int out_on_host, rpm_solve_info* info) {
   Ops ops{c};
   const rpm_options& o = c->opt;
-  const size_t F = c->fsz;
+  const size_t F = c->fst;
   float* epsb[2] = {c->fields, c->fields + F};
   float* xi[3] = {c->fields + 2 * F, c->fields + 3 * F, c->fields + 4 * F};
   float* D[2] = {c->fields + 5 * F, c->fields + 6 * F};
@@ -474,7 +479,7 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
   if (!ck(c, cudaMemsetAsync(ds, 0, kSmall * 8, c->st), "memset")) return RPM_ERR_CUDA;
   float* eps_cur = epsb[0];
   if (eps0) {
-    if (!ck(c, cudaMemcpyAsync(eps_cur, eps0, F * 4, cudaMemcpyDeviceToDevice, c->st), "eps0"))
+    if (!ck(c, cudaMemcpyAsync(eps_cur, eps0, c->fsz * 4, cudaMemcpyDeviceToDevice, c->st), "eps0"))
       return RPM_ERR_CUDA;
   } else if (++c->launches, !ck(c, launch_fill(eps_cur, E, c->n, c->st), "fill")) {
     return RPM_ERR_CUDA;
@@ -634,7 +639,7 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
   }
 
   // outputs: eps, sigma = C : eps, <sigma>
-  const size_t fb = F * sizeof(float);
+  const size_t fb = c->fsz * sizeof(float);
   if (eps_out) {
     if (!ck(c, cudaMemcpyAsync(eps_out, eps_cur, fb,
                                out_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->st),

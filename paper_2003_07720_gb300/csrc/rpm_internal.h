@@ -5,6 +5,8 @@
 
 namespace rpm {
 
+constexpr int kMaxBasis = 256;   // largest unstable basis (projections run in chunks of 32)
+
 // How the zero frequency and the input are treated by one Gamma0 application.
 enum GammaMode {
   GM_FULL_MAP = 0,   // input eps; output F(eps) = E - Gamma0 * ((C - C0) : eps)
@@ -45,6 +47,8 @@ bool grid_supported(int nx, int ny, int nz);
 // ---- field kernels (field_kernels.cu) -------------------------------------
 // Partial sums per block, then one finishing block; see the definitions.
 int dots_blocks_for(long long n);
+int dots_launches(int K);
+int combine_launches(int K);
 int stress_blocks_for(long long n);
 cudaError_t launch_dots(const float* x, const float* x_minus /*nullable*/, const float* Y,
                         long long ystride, int K, long long n, double* partials, int nblk,

@@ -1,0 +1,40 @@
+"""Write the stored oracle results used by the GPU tests and the benchmark's
+reference arm.  Calls only oracle/ (and the seeded input generators).
+
+  python tests/golden/make_golden.py softincl128    # ~2-3 h on one core
+"""
+from __future__ import annotations
+
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+import microstructure as ms  # noqa: E402
+from oracle import rpm_oracle as o  # noqa: E402
+
+
+def softincl128():
+    """Oracle RPM solve of the 128^3 benchmark cell (RSA spheres, seed 0,
+    inclusion E = 1e-3, C0 = matrix, e1 (x) e1, tol 1e-6, p_max 20, n_max 10)."""
+    cell = ms.cell_nearvoid(128, 0, c0_scale=1.0, e_incl=1e-3)
+    prob = o.Problem.from_cell(cell)
+    E = ms.unit_strain(0)
+    t0 = time.time()
+    r = o.rpm_solve(prob, E, o.Options(tol=1e-6, p_max=20, n_max=10, max_iters=5000))
+    out = {"workload": "softincl128 seed 0, E_incl 1e-3, C0 = matrix, E = e11, tol 1e-6, "
+                       "p_max 20, n_max 10",
+           "status": r.status, "iters": r.iters, "f_applies": r.f_applies, "basis": r.basis,
+           "residual": r.residual, "mean_stress": list(map(float, r.mean_stress)),
+           "growth_iters": r.growth_iters, "seconds_one_core": time.time() - t0,
+           "residuals_every_10": [float(v) for v in r.residuals[::10]]}
+    with open(os.path.join(HERE, "nearvoid128_oracle_solve.json"), "w") as f:
+        json.dump(out, f, indent=1)
+
+
+if __name__ == "__main__":
+    {"softincl128": softincl128}[sys.argv[1]]()

@@ -62,7 +62,7 @@ def test_host_side_checks(L):
     st = L.rpm_create(ctypes.byref(g), ctypes.cast(ph, ctypes.c_void_p), 0, 1, iso,
                       rpm.rpm_iso(1.0, -1.0), None, None, ctypes.byref(h))
     assert st == rpm.RPM_ERR_INVALID_ARG
-    bad = rpm.rpm_default_options(p_max=33)
+    bad = rpm.rpm_default_options(p_max=257)
     st = L.rpm_create(ctypes.byref(g), ctypes.cast(ph, ctypes.c_void_p), 0, 1, iso,
                       rpm.rpm_iso(1.0, 1.0), ctypes.byref(bad), None, ctypes.byref(h))
     assert st == rpm.RPM_ERR_INVALID_ARG

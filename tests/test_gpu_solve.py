@@ -86,20 +86,42 @@ def test_laminate_closed_form_on_gpu(rpm):
     assert np.max(np.abs(C - ref)) < CEFF_TOL * np.max(np.abs(ref))
 
 
-def test_nearvoid_128_solution_is_fixed_point(rpm):
-    """128^3 near-void cell (the benchmark workload): the GPU solution is a
-    fixed point of the oracle's F to the solver tolerance (FP64 check)."""
-    cell = ms.cell_nearvoid(128, 0)
+def test_softincl_128_solution_is_fixed_point(rpm):
+    """128^3 RSA cell of the benchmark (inclusion E = 1e-3): the GPU solution
+    is a fixed point of the oracle's F to the solver tolerance (FP64 check)."""
+    cell = ms.cell_nearvoid(128, 0, e_incl=1e-3)
     prob = o.Problem.from_cell(cell)
     E = ms.unit_strain(0)
     eps = torch.empty((6,) + cell.shape, device="cuda")
     with rpm.Context(cell, rpm.rpm_default_options(tol=1e-6, p_max=20)) as ctx:
         st, info = ctx.solve(E, eps_out=eps)
-    assert info["converged"]
+    assert info["converged"] and info["basis_size"] > 0
     e = eps.cpu().numpy().astype(np.float64)
     r = o.residual(prob, o.apply_F(prob, e, E), e, E)
     assert r < 2e-6, r
     assert np.max(np.abs(e.reshape(6, -1).mean(1) - E)) < 1e-5
+    s = o.stress(prob, e).reshape(6, -1).mean(1)
+    assert np.max(np.abs(s - np.array(info["mean_stress"]))) < 1e-6
+
+
+def test_nearvoid_trajectory_matches_oracle(rpm):
+    """Near-void cell (E_incl = 1e-6) at 32^3: Algorithm 2 stalls far above
+    1e-6 on both sides, and the GPU residual history follows the FP64
+    oracle's step by step (same basis growth, same residuals)."""
+    cell = ms.cell_nearvoid(32, 0)
+    prob = o.Problem.from_cell(cell)
+    E = ms.unit_strain(0)
+    steps = 150
+    r = o.rpm_solve(prob, E, o.Options(tol=1e-6, p_max=20, max_iters=steps))
+    with rpm.Context(cell, rpm.rpm_default_options(tol=1e-6, p_max=20, max_iters=steps)) as ctx:
+        res, ps = ctx.trace(steps + 1)
+        st, info = ctx.solve(E, raise_on_failure=False)
+    assert st == rpm.RPM_ERR_NOT_CONVERGED and r.status == "not_converged"
+    assert info["basis_size"] == r.basis
+    got = res[:steps + 1]
+    ref = np.array(r.residuals[:steps + 1])
+    assert np.max(np.abs(got - ref) / ref) < 2e-2
+    assert got[-1] > 1e-4
 
 
 def test_failure_paths(rpm):
