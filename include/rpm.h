@@ -143,6 +143,38 @@ rpm_status rpm_apply_gamma(rpm_ctx* ctx, const float* in, const double E[6], flo
                            int flags);
 
 /*
+ * rpm_apply_gamma without a context and without any device allocation.
+ * (The paper has no counterpart: this is a deployment variant of
+ * rpm_apply_gamma.)
+ *
+ * For callers that cannot call cudaMalloc: an application that owns all
+ * device memory through its own pool or plug-in allocator, or a loop that may
+ * not pay cudaMalloc's implicit device synchronisation.  It computes exactly
+ * what rpm_apply_gamma computes for the same grid, phases, C0, input, E and
+ * flags, but its scratch (the half spectrum and the FFT/frequency/material
+ * tables) is a set of fixed-size file-scope device arrays that every GPU
+ * loading the library holds until the process exits (about 6.6 MB).
+ *   grid     nx == ny <= 64 and nz <= 64 (and supported as above);
+ *            larger grids return RPM_ERR_UNSUPPORTED_GRID.
+ *   phase    DEVICE pointer, uint8 [nz][ny][nx], ids < n_phases.
+ *   phases   host array of n_phases (1..256) moduli; c0 the reference medium.
+ *   in, out  device fields [6][n] (may not alias); E host double[6]
+ *            (required for RPM_GAMMA_FULL_MAP); flags as rpm_apply_gamma.
+ *   cuda_stream  stream for the copies and kernels (NULL: legacy stream).
+ * The first call on a device looks up the arrays' device addresses; make that
+ * first call before any stream capture.  Each call copies its tables into
+ * the shared arrays and waits for those copies, then launches the kernels
+ * asynchronously.  All calls share the arrays, which keep the last call's
+ * contents: calls whose kernels overlap on a GPU (other streams, other host
+ * threads) race and must be serialised by the caller.
+ * Returns RPM_ERR_INVALID_ARG / RPM_ERR_UNSUPPORTED_GRID for bad arguments,
+ * RPM_ERR_CUDA if a CUDA call fails.
+ */
+rpm_status rpm_apply_gamma_noalloc(const rpm_grid* grid, const uint8_t* phase, int n_phases,
+                                   const rpm_iso* phases, rpm_iso c0, const float* in,
+                                   const double E[6], float* out, int flags, void* cuda_stream);
+
+/*
  * Solve the cell problem for macroscopic strain E (Algorithm 2; Algorithm 1
  * when p_max = 0).
  *   E          host double[6].
