@@ -88,6 +88,7 @@ typedef struct {
   float gamma_ms;      /* with opt.profile: summed device time of the Gamma0 applications */
   float proj_ms;       /* with opt.profile: summed time of the projection/combine kernels */
   long long launches;  /* CUDA kernels launched by the solve */
+  double proj_bytes;   /* algorithmic bytes moved by the projection/combine kernels */
 } rpm_solve_info;
 
 /* Fill `opt` with the defaults listed above. */

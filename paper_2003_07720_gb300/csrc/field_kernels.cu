@@ -14,7 +14,7 @@
 namespace rpm {
 
 constexpr int kRedThreads = 256;
-constexpr int kPerThread = 8;        // float4 per thread per dot pass (32 products)
+constexpr int kPerThread = 16;       // float4 per thread per dot pass (64 products)
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -33,8 +33,9 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // shuffle tree is a TwoSum, so the rounding errors of the float32 tree are
 // carried exactly in lo (float64 arithmetic is slow on this part; the pair
 // gives about 48 significant bits).
-__device__ __forceinline__ double warp_sum_compensated(float v) {
-  float hi = v, lo = 0.f;
+__device__ __forceinline__ void warp_sum_compensated(float v, float& hi, float& lo) {
+  hi = v;
+  lo = 0.f;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
@@ -44,7 +45,6 @@ __device__ __forceinline__ double warp_sum_compensated(float v) {
     hi = s;
     lo = lo + olo + e;
   }
-  return (double)hi + (double)lo;
 }
 
 // Block-reduce M float values per thread (acc) into partials[row(j) * nblk + blockIdx.x],
@@ -58,8 +58,9 @@ __device__ __forceinline__ void block_store(const float* acc, int m, int row0, d
 #pragma unroll
   for (int j = 0; j < M; ++j) {
     if (j < m) {
-      const double s = warp_sum_compensated(acc[j]);
-      if (lane == 0) red[warp][j] = s;
+      float hi, lo;
+      warp_sum_compensated(acc[j], hi, lo);
+      if (lane == 0) red[warp][j] = (double)hi + (double)lo;
     }
   }
   __syncthreads();

@@ -62,6 +62,7 @@ struct rpm_ctx {
   std::vector<double> H;             // host copy of H = Z^T F_u Z (row-major, p x p)
   int p = 0;
   long long launches = 0;            // kernels launched by the current solve
+  double proj_bytes = 0;             // algorithmic bytes of the projection kernels
   // event pairs for opt.profile: (start, stop, category 0 = Gamma0, 1 = projections)
   std::vector<cudaEvent_t> prof_ev;
   std::vector<int> prof_cat;
@@ -174,6 +175,7 @@ struct Ops {
   bool dots(const float* x, const float* xm, const float* Y, int K, double* sums) {
     const size_t m = mark(1);
     c->launches += 1 + dots_launches(K);
+    c->proj_bytes += (double)(K + 1 + (xm ? 1 : 0)) * (double)c->fsz * 4.0;
     bool ok = ck(c, launch_dots(x, xm, Y, (long long)c->fst, K, c->n, c->partials, c->nblk, c->st),
                  "dots") &&
               ck(c, launch_reduce_partials(c->partials, c->nblk, K + 1, sums, c->st), "reduce");
@@ -184,6 +186,7 @@ struct Ops {
                float cscale) {
     const size_t m = mark(1);
     c->launches += combine_launches(K);
+    c->proj_bytes += (double)(K + (x ? 1 : 0) + 1) * (double)c->fsz * 4.0;
     const bool ok =
         ck(c, launch_combine(out, x, xs, Y, (long long)c->fst, K, coef, cscale, c->n, c->st),
            "combine");
@@ -470,6 +473,7 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
   inf.status = RPM_OK;
   c->p = 0;
   c->launches = 0;
+  c->proj_bytes = 0;
   c->prof_used = 0;
   c->H.clear();
   std::vector<double> M;
@@ -668,6 +672,7 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
     (c->prof_cat[i] == 0 ? inf.gamma_ms : inf.proj_ms) += t;
   }
   inf.launches = c->launches;
+  inf.proj_bytes = c->proj_bytes;
   inf.iters = it;
   inf.gamma_applies = nF;
   inf.basis_size = c->p;

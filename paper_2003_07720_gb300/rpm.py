@@ -54,7 +54,8 @@ class rpm_solve_info(ctypes.Structure):
                 ("status", ctypes.c_int), ("residual", ctypes.c_double),
                 ("residual0", ctypes.c_double), ("mean_stress", ctypes.c_double * 6),
                 ("ms", ctypes.c_float), ("gamma_ms", ctypes.c_float),
-                ("proj_ms", ctypes.c_float), ("launches", ctypes.c_longlong)]
+                ("proj_ms", ctypes.c_float), ("launches", ctypes.c_longlong),
+                ("proj_bytes", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {"iters": self.iters, "gamma_applies": self.gamma_applies,
@@ -62,7 +63,7 @@ class rpm_solve_info(ctypes.Structure):
                 "status": self.status, "residual": self.residual,
                 "residual0": self.residual0, "mean_stress": list(self.mean_stress),
                 "ms": self.ms, "gamma_ms": self.gamma_ms, "proj_ms": self.proj_ms,
-                "launches": self.launches}
+                "launches": self.launches, "proj_bytes": self.proj_bytes}
 
 
 _lib = None
