@@ -10,7 +10,7 @@
  * Conventions shared by every entry point
  * ---------------------------------------
  * - A grid is nx * ny * nz voxels (x fastest), unit cell lengths lx, ly, lz.
- *   This build supports nx == ny in {4, 8, 16, 32, 64, 128} and
+ *   This build supports nx, ny in {4, 8, 16, 32, 64, 128, 256} and
  *   nz in {1, 2, 4, ..., 256}; nz = 1 is a 2D plane-strain cell.  Other
  *   grids return RPM_ERR_UNSUPPORTED_GRID.
  * - A field is float32 [6][nz][ny][nx]: the symmetric tensor components

@@ -14,6 +14,8 @@ heterogeneous materials using the recursive projection method", CMAME 2020):
   equilibrium error.
 * Section 3, Eqs. (3.1)-(3.13) and Algorithm 2: the recursive projection
   method wrapped around the fixed-point map F of Eq. (3.9).
+* Section 5.5, Algorithm 3: the polarization-based (Accelerated for
+  alpha = beta = 2) fixed-point map, alone or wrapped by RPM.
 
 A library FFT (numpy.fft) serves as the Fourier transform step; everything
 else is written out in plain numpy, in float64, with no blocking or fusion.
@@ -39,7 +41,9 @@ repository's design notes):
   is reported as a diagnostic;
 * "T11 >> T22" of Eq. (3.8) is read as |T22| <= kappa |T11| with
   kappa = 0.1; the basis is capped at p_max vectors; the iteration counter
-  nu counts fixed-point steps since the last basis growth.
+  nu counts fixed-point steps since the last basis growth;
+* Algorithm 3's s_b is read as alpha sigma - beta C0 : eps (the printed plus
+  sign does not keep the solution a fixed point).
 
 Parity: every function here is pinned by tests under tests/ against closed
 forms, brute-force solves, invariants or library routines.
@@ -269,6 +273,50 @@ def apply_F_classical(prob: Problem, eps: np.ndarray, E) -> np.ndarray:
     return ifft_fields(out, prob.shape)
 
 
+def apply_F_polarization(prob: Problem, eps: np.ndarray, E, alpha: float = 2.0,
+                         beta: float = 2.0) -> np.ndarray:
+    """Algorithm 3 (polarization-based scheme; alpha = beta = 2 is the
+    Accelerated scheme), Section 5.5, with s_b read as alpha sigma - beta C0 eps.
+
+    Steps in the algorithm's order:
+      sigma = C : eps;  s_a = sigma + (1 - beta) C0 : eps;
+      s_b = alpha sigma - beta C0 : eps;
+      eps_b_hat = -Gamma0_hat : s_b_hat (k != 0),  eps_b_hat(0) = beta E;
+      eps_next = (C + C0)^-1 : (s_a + C0 : eps_b).
+    (The listing prints s_b = alpha sigma + beta C0 eps; with that sign the
+    cell-problem solution is not a fixed point, so the minus sign is taken.)"""
+    E = np.asarray(E, float)
+    c0 = Problem(phase=np.zeros(prob.shape, np.uint8), lam=np.array([prob.lam0]),
+                 mu=np.array([prob.mu0]), lam0=0.0, mu0=0.0, lengths=prob.lengths,
+                 nyquist=prob.nyquist)
+    sig = stress(prob, eps)
+    c0eps = stress(c0, eps)
+    s_a = sig + (1.0 - beta) * c0eps
+    s_b = alpha * sig - beta * c0eps
+    sh = fft_fields(s_b)
+    eh = -gamma_hat_apply(prob, sh)
+    eh[:, 0, 0, 0] = beta * E * prob.n
+    eps_b = ifft_fields(eh, prob.shape)
+    t = s_a + stress(c0, eps_b)
+    # (C + C0)^-1 of an isotropic stiffness (lam_s, mu_s):
+    #   X = (t - lam_s / (3 lam_s + 2 mu_s) tr(t) I) / (2 mu_s)
+    lam_s = prob.lam[prob.phase] + prob.lam0
+    mu_s = prob.mu[prob.phase] + prob.mu0
+    tr = t[0] + t[1] + t[2]
+    out = t.copy()
+    out[:3] -= (lam_s / (3.0 * lam_s + 2.0 * mu_s) * tr)[None]
+    return out / (2.0 * mu_s)[None]
+
+
+def fixed_point_map(prob: Problem, opts):
+    """The map F of Algorithm 1/2 for opts.scheme: 'basic' (Eq. 3.9) or
+    'polarization' (Algorithm 3 with opts.alpha, opts.beta)."""
+    if getattr(opts, "scheme", "basic") == "polarization":
+        a, b = opts.alpha, opts.beta
+        return lambda eps, E: apply_F_polarization(prob, eps, E, a, b)
+    return lambda eps, E: apply_F(prob, eps, E)
+
+
 def uniform(E, shape) -> np.ndarray:
     return np.broadcast_to(np.asarray(E, float).reshape(6, 1, 1, 1), (6,) + tuple(shape)).copy()
 
@@ -310,6 +358,9 @@ class Options:
     p_max: int = 20
     kappa: float = 0.1          # |T22| <= kappa |T11|  ->  add one vector
     diverge_factor: float = 1e10
+    scheme: str = "basic"       # or "polarization" (Algorithm 3)
+    alpha: float = 2.0
+    beta: float = 2.0
 
 
 @dataclasses.dataclass
@@ -335,8 +386,9 @@ def basic_solve(prob: Problem, E, opts: Options | None = None, eps0=None) -> Res
     """Algorithm 1: eps^0 = E, eps^{i+1} = F(eps^i) until the increment
     residual is below tol."""
     opts = opts or Options()
+    F = fixed_point_map(prob, opts)
     eps = uniform(E, prob.shape) if eps0 is None else np.array(eps0, float)
-    xi = apply_F(prob, eps, E)
+    xi = F(eps, E)
     nF = 1
     r = residual(prob, xi, eps, E)
     r0 = r
@@ -346,7 +398,7 @@ def basic_solve(prob: Problem, E, opts: Options | None = None, eps0=None) -> Res
         if it >= opts.max_iters:
             return _finish(prob, Result(eps, False, "not_converged", it, nF, 0, r, hist))
         eps = xi
-        xi = apply_F(prob, eps, E)
+        xi = F(eps, E)
         nF += 1
         it += 1
         r = residual(prob, xi, eps, E)
@@ -356,8 +408,10 @@ def basic_solve(prob: Problem, E, opts: Options | None = None, eps0=None) -> Res
     return _finish(prob, Result(eps, True, "ok", it, nF, 0, r, hist))
 
 
-def apply_F_linear(prob: Problem, u: np.ndarray) -> np.ndarray:
+def apply_F_linear(prob: Problem, u: np.ndarray, opts=None) -> np.ndarray:
     """Jacobian F_u applied to u: F(u) with E = 0 (F is affine)."""
+    if opts is not None and getattr(opts, "scheme", "basic") == "polarization":
+        return apply_F_polarization(prob, u, np.zeros(6), opts.alpha, opts.beta)
     return apply_gamma_raw(prob, polarization(prob, u))
 
 
@@ -400,7 +454,7 @@ def _grow_basis(prob, st: RPMState, hist, opts: Options) -> int:
             continue
         u = u / nu_
         st.Z.append(u)
-        st.FZ.append(apply_F_linear(prob, u))
+        st.FZ.append(apply_F_linear(prob, u, opts))
         added += 1
     p = len(st.Z)
     st.H = np.array([[inner(st.Z[i], st.FZ[j]) for j in range(p)] for i in range(p)])
@@ -416,9 +470,10 @@ def rpm_solve(prob: Problem, E, opts: Options | None = None, eps0=None) -> Resul
     fixed-point steps since the last growth the basis grows.
     """
     opts = opts or Options()
+    F = fixed_point_map(prob, opts)
     E = np.asarray(E, float)
     eps = uniform(E, prob.shape) if eps0 is None else np.array(eps0, float)
-    xi = apply_F(prob, eps, E)
+    xi = F(eps, E)
     nF = 1
     st = RPMState([], [], np.zeros((0, 0)))
     hist = [xi]
@@ -441,7 +496,7 @@ def rpm_solve(prob: Problem, E, opts: Options | None = None, eps0=None) -> Resul
                 eps += (zp[j] - zeta[j]) * st.Z[j]
         else:
             eps = xi
-        xi = apply_F(prob, eps, E)
+        xi = F(eps, E)
         nF += 1
         it += 1
         nu += 1
@@ -532,7 +587,7 @@ def hashin_shtrikman(f1, K1, G1, K2, G2):
     return Kl, Ku, Gl, Gu
 
 
-def dense_linear_operator(prob: Problem) -> np.ndarray:
+def dense_linear_operator(prob: Problem, opts=None) -> np.ndarray:
     """Dense matrix of F_u on R^(6n) (stored components), built column by
     column by applying F with E = 0 to unit vectors (tiny grids only)."""
     N = 6 * prob.n
@@ -540,5 +595,5 @@ def dense_linear_operator(prob: Problem) -> np.ndarray:
     for k in range(N):
         e = np.zeros(N)
         e[k] = 1.0
-        L[:, k] = apply_F_linear(prob, e.reshape((6,) + prob.shape)).ravel()
+        L[:, k] = apply_F_linear(prob, e.reshape((6,) + prob.shape), opts).ravel()
     return L

@@ -14,7 +14,7 @@
 namespace rpm {
 
 constexpr int kRedThreads = 256;
-constexpr int kPerThread = 16;       // float4 per thread per dot pass (64 products)
+constexpr int kPerThread = 8;        // float4 per thread per dot pass (32 products)
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

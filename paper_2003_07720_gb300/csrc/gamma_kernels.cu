@@ -310,6 +310,150 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(GridDev g, float2* __restri
 }
 
 // ---------------------------------------------------------------------------
+// Five-pass variant for planes that do not fit in shared memory (nx = 256)
+// and for nx != ny: rows along x, pencils along y, the z pass above, pencils
+// along y (inverse), rows along x (inverse).  The spectrum layout and slot
+// orders are those of the three-pass path, so pass B is shared.
+// ---------------------------------------------------------------------------
+constexpr int kRows = 16;             // rows per block in the x passes
+constexpr int kRowsP = kRows + 1;     // odd stride
+
+template <int NX>
+__global__ void __launch_bounds__(kThreads) k_rows_fwd(GridDev g, const float* __restrict__ in,
+                                                       float2* __restrict__ spec, int mode) {
+  constexpr int NXH = NX / 2, SX = NXH + 1;
+  extern __shared__ float2 sm[];
+  float2* P = sm;                                  // [SX][kRowsP]
+  float2* twx = P + SX * kRowsP;
+  float2* r2c = twx + NXH;
+  float2* dm = r2c + SX;
+  const int y0 = blockIdx.x * kRows, z = blockIdx.y, c = blockIdx.z;
+  const int ny = g.ny;
+  for (int i = threadIdx.x; i < NXH; i += blockDim.x) twx[i] = g.tw_x[i];
+  for (int i = threadIdx.x; i < SX; i += blockDim.x) r2c[i] = g.r2c_w[i];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) dm[i] = g.dmat[i];
+  __syncthreads();
+  const size_t n2 = (size_t)g.n / 2;
+  const size_t row2 = ((size_t)z * ny + y0) * NXH;         // float2 offset of row y0
+  const float2* in2 = reinterpret_cast<const float2*>(in);
+  const uchar2* ph2 = reinterpret_cast<const uchar2*>(g.phase) + row2;
+  constexpr int TOT = kRows * NXH;
+  for (int idx = threadIdx.x; idx < TOT; idx += kThreads) {
+    const int r = idx / NXH, h = idx - r * NXH;
+    float2 t = make_float2(0.f, 0.f);
+    if (y0 + r < ny) {
+      const size_t v = row2 + idx;
+      if (mode == GM_RAW_TAU) {
+        t = in2[c * n2 + v];
+      } else {
+        const uchar2 ph = ph2[idx];
+        const float2 d0 = dm[ph.x], d1 = dm[ph.y];
+        const float2 e = in2[c * n2 + v];
+        t = make_float2(2.f * d0.y * e.x, 2.f * d1.y * e.y);
+        if (c < 3) {
+          const float2 a = in2[v], b = in2[n2 + v], d = in2[2 * n2 + v];
+          t.x = fmaf(d0.x, a.x + b.x + d.x, t.x);
+          t.y = fmaf(d1.x, a.y + b.y + d.y, t.y);
+        }
+      }
+    }
+    P[h * kRowsP + r] = t;
+  }
+  __syncthreads();
+  smem_fft<NXH, false, kRows>(P, 1, kRowsP, twx);
+  for (int t = threadIdx.x; t < kRows * (NXH / 2 + 1); t += blockDim.x) {
+    const int r = t % kRows, k = t / kRows;
+    if (k == 0) {
+      const float2 z0 = P[r];
+      P[r] = make_float2(z0.x + z0.y, 0.f);
+      P[NXH * kRowsP + r] = make_float2(z0.x - z0.y, 0.f);
+    } else {
+      const int kk = NXH - k;
+      const int sk = slot_of<NXH>(k), skk = slot_of<NXH>(kk);
+      const float2 a = P[sk * kRowsP + r], b = P[skk * kRowsP + r];
+      P[sk * kRowsP + r] = r2c_post(a, b, r2c[k]);
+      if (kk != k) P[skk * kRowsP + r] = r2c_post(b, a, r2c[kk]);
+    }
+  }
+  __syncthreads();
+  float2* out = spec + ((size_t)c * g.nz + z) * g.plane + (size_t)y0 * SX;
+  for (int idx = threadIdx.x; idx < kRows * SX; idx += blockDim.x) {
+    const int r = idx / SX, sx = idx - r * SX;
+    if (y0 + r < ny) out[idx] = P[sx * kRowsP + r];
+  }
+}
+
+template <int NX>
+__global__ void __launch_bounds__(kThreads) k_rows_inv(GridDev g, const float2* __restrict__ spec,
+                                                       float* __restrict__ outp, float scale) {
+  constexpr int NXH = NX / 2, SX = NXH + 1;
+  extern __shared__ float2 sm[];
+  float2* P = sm;
+  float2* twx = P + SX * kRowsP;
+  float2* r2c = twx + NXH;
+  const int y0 = blockIdx.x * kRows, z = blockIdx.y, c = blockIdx.z;
+  const int ny = g.ny;
+  for (int i = threadIdx.x; i < NXH; i += blockDim.x) twx[i] = g.tw_x[i];
+  for (int i = threadIdx.x; i < SX; i += blockDim.x) r2c[i] = g.r2c_w[i];
+  const float2* src = spec + ((size_t)c * g.nz + z) * g.plane + (size_t)y0 * SX;
+  for (int idx = threadIdx.x; idx < kRows * SX; idx += blockDim.x) {
+    const int r = idx / SX, sx = idx - r * SX;
+    P[sx * kRowsP + r] = (y0 + r < ny) ? src[idx] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < kRows * (NXH / 2 + 1); t += blockDim.x) {
+    const int r = t % kRows, k = t / kRows;
+    if (k == 0) {
+      P[r] = c2r_pre(P[r], P[NXH * kRowsP + r], make_float2(1.f, 0.f));
+    } else {
+      const int kk = NXH - k;
+      const int sk = slot_of<NXH>(k), skk = slot_of<NXH>(kk);
+      const float2 a = P[sk * kRowsP + r], b = P[skk * kRowsP + r];
+      P[sk * kRowsP + r] = c2r_pre(a, b, r2c[k]);
+      if (kk != k) P[skk * kRowsP + r] = c2r_pre(b, a, r2c[kk]);
+    }
+  }
+  __syncthreads();
+  smem_fft<NXH, true, kRows>(P, 1, kRowsP, twx);
+  const size_t n2 = (size_t)g.n / 2;
+  float2* out2 = reinterpret_cast<float2*>(outp) + c * n2 + ((size_t)z * ny + y0) * NXH;
+  for (int idx = threadIdx.x; idx < kRows * NXH; idx += blockDim.x) {
+    const int r = idx / NXH, h = idx - r * NXH;
+    if (y0 + r < ny) out2[idx] = cscale(P[h * kRowsP + r], scale);
+  }
+}
+
+// In-place FFT along y of TY consecutive x slots of one (component, z) plane.
+template <int NY>
+struct YPencilCfg {
+  static constexpr int TY = NY >= 256 ? 16 : (NY >= 128 ? 32 : 64);
+  static constexpr int NYP = NY + 1;
+};
+
+template <int NY, bool INV>
+__global__ void __launch_bounds__(kThreads) k_ypencil(GridDev g, float2* __restrict__ spec) {
+  using C = YPencilCfg<NY>;
+  constexpr int TY = C::TY, NYP = C::NYP;
+  extern __shared__ float2 sm[];
+  float2* B = sm;                  // [TY][NYP]
+  float2* twy = B + TY * NYP;
+  for (int i = threadIdx.x; i < NY; i += blockDim.x) twy[i] = g.tw_y[i];
+  const int sx0 = blockIdx.x * TY;
+  const int SX = g.nxh + 1;
+  float2* pl = spec + (size_t)blockIdx.y * g.plane;     // blockIdx.y = c * nz + z
+  for (int idx = threadIdx.x; idx < TY * NY; idx += blockDim.x) {
+    const int t = idx % TY, y = idx / TY;
+    B[t * NYP + y] = (sx0 + t < SX) ? pl[(size_t)y * SX + sx0 + t] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  smem_fft<NY, INV, TY>(B, NYP, 1, twy);
+  for (int idx = threadIdx.x; idx < TY * NY; idx += blockDim.x) {
+    const int t = idx % TY, y = idx / TY;
+    if (sx0 + t < SX) pl[(size_t)y * SX + sx0 + t] = B[t * NYP + y];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 template <typename K>
@@ -349,6 +493,67 @@ static cudaError_t launch_pencil_pass(const GridDev& g, float2* spec, int mode, 
   return cudaGetLastError();
 }
 
+template <int NX>
+static cudaError_t launch_rows(const GridDev& g, const float* in, float* out, float2* spec,
+                               int mode, int which, cudaStream_t st) {
+  constexpr int NXH = NX / 2, SX = NXH + 1;
+  const dim3 grid((g.ny + kRows - 1) / kRows, g.nz, 6);
+  if (which == 0) {
+    const size_t smem = (size_t)(SX * kRowsP + NXH + SX + 256) * sizeof(float2);
+    cudaError_t e = set_smem(k_rows_fwd<NX>, smem);
+    if (e != cudaSuccess) return e;
+    k_rows_fwd<NX><<<grid, kThreads, smem, st>>>(g, in, spec, mode);
+  } else {
+    const size_t smem = (size_t)(SX * kRowsP + NXH + SX) * sizeof(float2);
+    cudaError_t e = set_smem(k_rows_inv<NX>, smem);
+    if (e != cudaSuccess) return e;
+    k_rows_inv<NX><<<grid, kThreads, smem, st>>>(g, spec, out, 1.0f / (float)g.n);
+  }
+  return cudaGetLastError();
+}
+
+template <int NY>
+static cudaError_t launch_ypencil(const GridDev& g, float2* spec, bool inv, cudaStream_t st) {
+  using C = YPencilCfg<NY>;
+  const size_t smem = (size_t)(C::TY * C::NYP + NY) * sizeof(float2);
+  const dim3 grid((g.nxh + 1 + C::TY - 1) / C::TY, 6 * g.nz);
+  cudaError_t e;
+  if (inv) {
+    if ((e = set_smem(k_ypencil<NY, true>, smem)) != cudaSuccess) return e;
+    k_ypencil<NY, true><<<grid, kThreads, smem, st>>>(g, spec);
+  } else {
+    if ((e = set_smem(k_ypencil<NY, false>, smem)) != cudaSuccess) return e;
+    k_ypencil<NY, false><<<grid, kThreads, smem, st>>>(g, spec);
+  }
+  return cudaGetLastError();
+}
+
+#define RPM_SIZES(X) X(4) X(8) X(16) X(32) X(64) X(128) X(256)
+
+static cudaError_t dispatch_rows(const GridDev& g, const float* in, float* out, float2* spec,
+                                 int mode, int which, cudaStream_t st) {
+  switch (g.nx) {
+#define RPM_CASE(N) \
+  case N: return launch_rows<N>(g, in, out, spec, mode, which, st);
+    RPM_SIZES(RPM_CASE)
+#undef RPM_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+static cudaError_t dispatch_ypencil(const GridDev& g, float2* spec, bool inv, cudaStream_t st) {
+  switch (g.ny) {
+#define RPM_CASE(N) \
+  case N: return launch_ypencil<N>(g, spec, inv, st);
+    RPM_SIZES(RPM_CASE)
+#undef RPM_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// three-pass (whole xy planes in shared memory) when the plane fits
+static bool plane_fits(int nx, int ny) { return nx == ny && nx <= 128; }
+
 static cudaError_t dispatch_plane(const GridDev& g, const float* in, float* out, float2* spec,
                                   int mode, int which, cudaStream_t st) {
   switch (g.nx) {
@@ -378,12 +583,16 @@ static cudaError_t dispatch_pencil(const GridDev& g, float2* spec, int mode, con
   }
 }
 
+int gamma_launches(int nx, int ny) { return plane_fits(nx, ny) ? 3 : 5; }
+
+static bool xy_size_ok(int n) {
+  return n == 4 || n == 8 || n == 16 || n == 32 || n == 64 || n == 128 || n == 256;
+}
+
 bool grid_supported(int nx, int ny, int nz) {
-  if (nx != ny) return false;
-  const bool plane_ok = nx == 4 || nx == 8 || nx == 16 || nx == 32 || nx == 64 || nx == 128;
   const bool z_ok = nz == 1 || nz == 2 || nz == 4 || nz == 8 || nz == 16 || nz == 32 || nz == 64 ||
                     nz == 128 || nz == 256;
-  return plane_ok && z_ok;
+  return xy_size_ok(nx) && xy_size_ok(ny) && z_ok;
 }
 
 cudaError_t launch_apply_gamma(const GridDev& g, const float* in, float* out, float2* spec,
@@ -393,11 +602,17 @@ cudaError_t launch_apply_gamma(const GridDev& g, const float* in, float* out, fl
   const double l0 = g.lam0, m0 = g.mu0;
   ga.a = (float)((l0 + m0) / (l0 + 2.0 * m0));
   ga.inv_mu0 = (float)(1.0 / m0);
-  cudaError_t e = dispatch_plane(g, in, out, spec, mode, 0, st);
-  if (e != cudaSuccess) return e;
-  e = dispatch_pencil(g, spec, mode, ga, st);
-  if (e != cudaSuccess) return e;
-  return dispatch_plane(g, in, out, spec, mode, 1, st);
+  cudaError_t e;
+  if (plane_fits(g.nx, g.ny)) {
+    if ((e = dispatch_plane(g, in, out, spec, mode, 0, st)) != cudaSuccess) return e;
+    if ((e = dispatch_pencil(g, spec, mode, ga, st)) != cudaSuccess) return e;
+    return dispatch_plane(g, in, out, spec, mode, 1, st);
+  }
+  if ((e = dispatch_rows(g, in, out, spec, mode, 0, st)) != cudaSuccess) return e;
+  if ((e = dispatch_ypencil(g, spec, false, st)) != cudaSuccess) return e;
+  if ((e = dispatch_pencil(g, spec, mode, ga, st)) != cudaSuccess) return e;
+  if ((e = dispatch_ypencil(g, spec, true, st)) != cudaSuccess) return e;
+  return dispatch_rows(g, in, out, spec, mode, 1, st);
 }
 
 }  // namespace rpm

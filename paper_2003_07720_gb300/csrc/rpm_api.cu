@@ -166,7 +166,7 @@ struct Ops {
   }
   bool gamma(const float* in, float* out, const double* E, int mode) {
     const size_t m = mark(0);
-    c->launches += 3;
+    c->launches += gamma_launches(c->g.nx, c->g.ny);
     const bool ok = ck(c, launch_apply_gamma(c->g, in, out, c->spec, E, mode, c->st), "apply_gamma");
     done(m);
     return ok;

@@ -43,6 +43,7 @@ cudaError_t launch_apply_gamma(const GridDev& g, const float* in, float* out, fl
                                const double E[6], int mode, cudaStream_t st);
 
 bool grid_supported(int nx, int ny, int nz);
+int gamma_launches(int nx, int ny);   // kernels per Gamma0 application (3 or 5)
 
 // ---- field kernels (field_kernels.cu) -------------------------------------
 // Partial sums per block, then one finishing block; see the definitions.

@@ -47,7 +47,10 @@ def _run(cell, mode, nyq=0, seed=1, E=None):
 
 @pytest.mark.parametrize("shape", [(4, 4, 4), (8, 8, 8), (16, 16, 16), (32, 32, 32),
                                    (16, 8, 8), (2, 16, 16), (1, 32, 32), (64, 16, 16),
-                                   (8, 64, 64), (4, 128, 128), (256, 8, 8)])
+                                   (8, 64, 64), (4, 128, 128), (256, 8, 8),
+                                   # five-pass path: 256^2 planes and nx != ny
+                                   (4, 256, 256), (2, 256, 16), (16, 32, 64), (8, 16, 128),
+                                   (1, 8, 256), (32, 64, 32)])
 @pytest.mark.parametrize("mode", [0, 1, 2])
 def test_apply_gamma_matches_oracle(shape, mode):
     got, ref = _run(_cell(shape, 3), mode)

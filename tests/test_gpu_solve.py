@@ -86,6 +86,29 @@ def test_laminate_closed_form_on_gpu(rpm):
     assert np.max(np.abs(C - ref)) < CEFF_TOL * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("n,frac", [(256, 0.5), (256, 3 / 8)])
+def test_laminate_256_closed_form(rpm, n, frac):
+    """256^3 laminate (8 layer pairs along z, contrast 1e3, C0 at the mean):
+    the five-pass Gamma0 path at full size against the exact C_eff columns of
+    the two hardest loads (normal 33 and shear 13)."""
+    z = np.arange(n)
+    period = n // 8
+    lay = ((z % period) < round(frac * period)).astype(np.uint8)
+    phase = np.broadcast_to(lay[:, None, None], (n, n, n)).copy()
+    l0, m0 = ms.lame(1.0, 0.3)
+    l1, m1 = ms.lame(1e3, 0.3)
+    cell = ms.Cell(phase=phase, lam=np.array([l0, l1]), mu=np.array([m0, m1]),
+                   lam0=0.5 * (l0 + l1), mu0=0.5 * (m0 + m1))
+    f1 = float(lay.mean())
+    ref = o.laminate_ceff([1 - f1, f1], cell.lam, cell.mu)
+    with rpm.Context(cell, rpm.rpm_default_options(tol=1e-6, p_max=20)) as ctx:
+        for j in (2, 4):
+            st, info = ctx.solve(ms.unit_strain(j))
+            assert info["converged"]
+            col = np.array(info["mean_stress"])
+            assert np.max(np.abs(col - ref[:, j])) < CEFF_TOL * np.max(np.abs(ref)), (j, col, ref[:, j])
+
+
 def test_softincl_128_solution_is_fixed_point(rpm):
     """128^3 RSA cell of the benchmark (inclusion E = 1e-3): the GPU solution
     is a fixed point of the oracle's F to the solver tolerance (FP64 check)."""
