@@ -10,9 +10,10 @@
  * Conventions shared by every entry point
  * ---------------------------------------
  * - A grid is nx * ny * nz voxels (x fastest), unit cell lengths lx, ly, lz.
- *   This build supports nx, ny in {4, 8, 16, 32, 64, 128, 256} and
- *   nz in {1, 2, 4, ..., 256}; nz = 1 is a 2D plane-strain cell.  Other
- *   grids return RPM_ERR_UNSUPPORTED_GRID.
+ *   This build supports nx, ny in {4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128,
+ *   256} and nz in {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 256};
+ *   nz = 1 is a 2D plane-strain cell.  Other grids return
+ *   RPM_ERR_UNSUPPORTED_GRID.
  * - A field is float32 [6][nz][ny][nx]: the symmetric tensor components
  *   11, 22, 33, 23, 13, 12 (tensor components, not engineering shears).
  *   Field pointers are DEVICE pointers unless an argument says otherwise,

@@ -14,7 +14,7 @@
 // Keeping spectra in slot order means no permutation pass is ever needed:
 // the Green-operator step maps a slot to its frequency arithmetically.
 //
-// Register DFTs of length 1, 2, 4, 8, 16 are written out with exact
+// Register DFTs of length 1, 2, 3, 4, 6, 8, 12, 16 are written out with exact
 // constants; twiddles W_N^m come from host tables computed in double.
 #pragma once
 #include <cuda_runtime.h>
@@ -115,36 +115,99 @@ struct RegDft<8, INV> {
   }
 };
 
+constexpr float kSqrt3Half = 0.866025403784438646763723170753f;
+
+// exp(-+ 2 pi i m / 12): multiples of 30 degrees, exact constants
 template <bool INV>
-struct RegDft<16, INV> {
+__device__ __forceinline__ float2 w12(int m) {
+  float c, s;
+  switch (m % 12) {
+    case 0: c = 1.f; s = 0.f; break;
+    case 1: c = kSqrt3Half; s = 0.5f; break;
+    case 2: c = 0.5f; s = kSqrt3Half; break;
+    case 3: c = 0.f; s = 1.f; break;
+    case 4: c = -0.5f; s = kSqrt3Half; break;
+    case 5: c = -kSqrt3Half; s = 0.5f; break;
+    case 6: c = -1.f; s = 0.f; break;
+    case 7: c = -kSqrt3Half; s = -0.5f; break;
+    case 8: c = -0.5f; s = -kSqrt3Half; break;
+    case 9: c = 0.f; s = -1.f; break;
+    case 10: c = 0.5f; s = -kSqrt3Half; break;
+    default: c = kSqrt3Half; s = -0.5f; break;
+  }
+  return INV ? make_float2(c, s) : make_float2(c, -s);
+}
+
+template <bool INV>
+struct RegDft<3, INV> {
   __device__ __forceinline__ static void run(float2* v) {
-    float2 y[4][4];   // y[n2][k1]
+    const float2 a = v[0], b = v[1], c = v[2];
+    const float2 t = cadd(b, c);
+    const float2 m = make_float2(a.x - 0.5f * t.x, a.y - 0.5f * t.y);
+    const float2 d = make_float2(kSqrt3Half * (b.x - c.x), kSqrt3Half * (b.y - c.y));
+    v[0] = cadd(a, t);
+    // forward: X1 = m - i d, X2 = m + i d (inverse: the conjugate pattern)
+    v[1] = INV ? make_float2(m.x - d.y, m.y + d.x) : make_float2(m.x + d.y, m.y - d.x);
+    v[2] = INV ? make_float2(m.x + d.y, m.y - d.x) : make_float2(m.x - d.y, m.y + d.x);
+  }
+};
+
+// Two-level in-register DFT of length A * B: A-point DFTs over the stride-B
+// subsequences, twiddles W_(A B)^(n2 k1), B-point DFTs; natural output order.
+// TW(m) returns W_(A B)^m for the table used by the length.
+template <int A, int B, bool INV, int TWN>
+__device__ __forceinline__ void reg_dft_2level(float2* v) {
+  float2 y[B][A];
 #pragma unroll
-    for (int n2 = 0; n2 < 4; ++n2) {
-      float2 t[4] = {v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]};
-      RegDft<4, INV>::run(t);
+  for (int n2 = 0; n2 < B; ++n2) {
+    float2 t[A];
 #pragma unroll
-      for (int k1 = 0; k1 < 4; ++k1) y[n2][k1] = (n2 && k1) ? cmul(t[k1], w16<INV>(n2 * k1)) : t[k1];
-    }
+    for (int n1 = 0; n1 < A; ++n1) t[n1] = v[n1 * B + n2];
+    RegDft<A, INV>::run(t);
 #pragma unroll
-    for (int k1 = 0; k1 < 4; ++k1) {
-      float2 t[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
-      RegDft<4, INV>::run(t);
-#pragma unroll
-      for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[k2];
+    for (int k1 = 0; k1 < A; ++k1) {
+      if (n2 && k1) {
+        const float2 w = TWN == 16 ? w16<INV>(n2 * k1) : w12<INV>((12 / (A * B)) * n2 * k1);
+        y[n2][k1] = cmul(t[k1], w);
+      } else {
+        y[n2][k1] = t[k1];
+      }
     }
   }
+#pragma unroll
+  for (int k1 = 0; k1 < A; ++k1) {
+    float2 t[B];
+#pragma unroll
+    for (int n2 = 0; n2 < B; ++n2) t[n2] = y[n2][k1];
+    RegDft<B, INV>::run(t);
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) v[k1 + A * k2] = t[k2];
+  }
+}
+
+template <bool INV>
+struct RegDft<16, INV> {
+  __device__ __forceinline__ static void run(float2* v) { reg_dft_2level<4, 4, INV, 16>(v); }
+};
+template <bool INV>
+struct RegDft<6, INV> {
+  __device__ __forceinline__ static void run(float2* v) { reg_dft_2level<3, 2, INV, 12>(v); }
+};
+template <bool INV>
+struct RegDft<12, INV> {
+  __device__ __forceinline__ static void run(float2* v) { reg_dft_2level<4, 3, INV, 12>(v); }
 };
 
 // Split of a line length N = N1 * N2 into the two register steps.  One
 // definition serves device templates and host-side table builders.
+// Register DFT lengths: 1, 2, 3, 4, 6, 8, 12, 16.  Lines up to 256 = 2^a 3^b.
 __host__ __device__ constexpr int split_n1(int N) {
-  return N <= 16 ? N : (N == 32 ? 8 : (N == 64 ? 8 : 16));
+  return N <= 16 ? N : (N == 24 || N == 32 || N == 64 ? 8 : 16);
 }
 __host__ __device__ constexpr int split_n2(int N) { return N / split_n1(N); }
 __host__ __device__ constexpr bool fft_size_ok(int N) {
-  return N == 1 || N == 2 || N == 4 || N == 8 || N == 16 || N == 32 || N == 64 || N == 128 ||
-         N == 256;
+  return N == 1 || N == 2 || N == 3 || N == 4 || N == 6 || N == 8 || N == 12 || N == 16 ||
+         N == 24 || N == 32 || N == 48 || N == 64 || N == 96 || N == 128 || N == 256;
 }
 
 template <int N>

@@ -528,7 +528,9 @@ static cudaError_t launch_ypencil(const GridDev& g, float2* spec, bool inv, cuda
   return cudaGetLastError();
 }
 
-#define RPM_SIZES(X) X(4) X(8) X(16) X(32) X(64) X(128) X(256)
+#define RPM_SIZES(X) X(4) X(6) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(256)
+#define RPM_Z_SIZES(X) \
+  X(1) X(2) X(3) X(4) X(6) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(256)
 
 static cudaError_t dispatch_rows(const GridDev& g, const float* in, float* out, float2* spec,
                                  int mode, int which, cudaStream_t st) {
@@ -554,15 +556,35 @@ static cudaError_t dispatch_ypencil(const GridDev& g, float2* spec, bool inv, cu
 // three-pass (whole xy planes in shared memory) when the plane fits
 static bool plane_fits(int nx, int ny) { return nx == ny && nx <= 128; }
 
+static bool xy_size_ok(int n) {
+  switch (n) {
+#define RPM_CASE(N) case N:
+    RPM_SIZES(RPM_CASE)
+#undef RPM_CASE
+    return true;
+    default: return false;
+  }
+}
+
+static bool z_size_ok(int n) {
+  switch (n) {
+#define RPM_CASE(N) case N:
+    RPM_Z_SIZES(RPM_CASE)
+#undef RPM_CASE
+    return true;
+    default: return false;
+  }
+}
+
+#define RPM_PLANE_SIZES(X) X(4) X(6) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128)
+
 static cudaError_t dispatch_plane(const GridDev& g, const float* in, float* out, float2* spec,
                                   int mode, int which, cudaStream_t st) {
   switch (g.nx) {
-    case 4: return launch_plane_passes<4>(g, in, out, spec, mode, which, st);
-    case 8: return launch_plane_passes<8>(g, in, out, spec, mode, which, st);
-    case 16: return launch_plane_passes<16>(g, in, out, spec, mode, which, st);
-    case 32: return launch_plane_passes<32>(g, in, out, spec, mode, which, st);
-    case 64: return launch_plane_passes<64>(g, in, out, spec, mode, which, st);
-    case 128: return launch_plane_passes<128>(g, in, out, spec, mode, which, st);
+#define RPM_CASE(N) \
+  case N: return launch_plane_passes<N>(g, in, out, spec, mode, which, st);
+    RPM_PLANE_SIZES(RPM_CASE)
+#undef RPM_CASE
     default: return cudaErrorInvalidValue;
   }
 }
@@ -570,29 +592,18 @@ static cudaError_t dispatch_plane(const GridDev& g, const float* in, float* out,
 static cudaError_t dispatch_pencil(const GridDev& g, float2* spec, int mode, const GammaArgs& ga,
                                    cudaStream_t st) {
   switch (g.nz) {
-    case 1: return launch_pencil_pass<1>(g, spec, mode, ga, st);
-    case 2: return launch_pencil_pass<2>(g, spec, mode, ga, st);
-    case 4: return launch_pencil_pass<4>(g, spec, mode, ga, st);
-    case 8: return launch_pencil_pass<8>(g, spec, mode, ga, st);
-    case 16: return launch_pencil_pass<16>(g, spec, mode, ga, st);
-    case 32: return launch_pencil_pass<32>(g, spec, mode, ga, st);
-    case 64: return launch_pencil_pass<64>(g, spec, mode, ga, st);
-    case 128: return launch_pencil_pass<128>(g, spec, mode, ga, st);
-    case 256: return launch_pencil_pass<256>(g, spec, mode, ga, st);
+#define RPM_CASE(N) \
+  case N: return launch_pencil_pass<N>(g, spec, mode, ga, st);
+    RPM_Z_SIZES(RPM_CASE)
+#undef RPM_CASE
     default: return cudaErrorInvalidValue;
   }
 }
 
 int gamma_launches(int nx, int ny) { return plane_fits(nx, ny) ? 3 : 5; }
 
-static bool xy_size_ok(int n) {
-  return n == 4 || n == 8 || n == 16 || n == 32 || n == 64 || n == 128 || n == 256;
-}
-
 bool grid_supported(int nx, int ny, int nz) {
-  const bool z_ok = nz == 1 || nz == 2 || nz == 4 || nz == 8 || nz == 16 || nz == 32 || nz == 64 ||
-                    nz == 128 || nz == 256;
-  return xy_size_ok(nx) && xy_size_ok(ny) && z_ok;
+  return xy_size_ok(nx) && xy_size_ok(ny) && z_size_ok(nz);
 }
 
 cudaError_t launch_apply_gamma(const GridDev& g, const float* in, float* out, float2* spec,

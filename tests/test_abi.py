@@ -47,10 +47,12 @@ def test_host_side_checks(L):
     assert (o.n_max, o.p_max, o.max_iters) == (10, 20, 5000) and o.tol == 1e-6
     assert rpm.rpm_grid_supported(128, 128, 128)
     assert rpm.rpm_grid_supported(64, 64, 1)
-    assert not rpm.rpm_grid_supported(96, 96, 96)
-    assert not rpm.rpm_grid_supported(64, 32, 32)
+    assert rpm.rpm_grid_supported(96, 96, 96)
+    assert not rpm.rpm_grid_supported(80, 80, 80)
+    assert rpm.rpm_grid_supported(64, 32, 32)
+    assert not rpm.rpm_grid_supported(512, 512, 8)
     h = ctypes.c_void_p()
-    g = rpm.rpm_grid(48, 48, 48, 1.0, 1.0, 1.0)
+    g = rpm.rpm_grid(40, 40, 40, 1.0, 1.0, 1.0)
     iso = (rpm.rpm_iso * 1)(rpm.rpm_iso(1.0, 1.0))
     ph = (ctypes.c_uint8 * (48 ** 3))()
     st = L.rpm_create(ctypes.byref(g), ctypes.cast(ph, ctypes.c_void_p), 0, 1, iso,

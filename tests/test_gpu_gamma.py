@@ -50,7 +50,10 @@ def _run(cell, mode, nyq=0, seed=1, E=None):
                                    (8, 64, 64), (4, 128, 128), (256, 8, 8),
                                    # five-pass path: 256^2 planes and nx != ny
                                    (4, 256, 256), (2, 256, 16), (16, 32, 64), (8, 16, 128),
-                                   (1, 8, 256), (32, 64, 32)])
+                                   (1, 8, 256), (32, 64, 32),
+                                   # radix-3 lengths (2^a 3^b)
+                                   (48, 48, 48), (96, 96, 96), (12, 24, 24), (6, 12, 12),
+                                   (3, 48, 48), (24, 6, 6), (16, 96, 48), (8, 96, 256)])
 @pytest.mark.parametrize("mode", [0, 1, 2])
 def test_apply_gamma_matches_oracle(shape, mode):
     got, ref = _run(_cell(shape, 3), mode)

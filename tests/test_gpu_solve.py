@@ -60,6 +60,24 @@ def test_rpm_iteration_count_tracks_oracle(rpm, sphere32):
     assert abs(info["iters"] - r.iters) <= max(3, r.iters // 5), (info, r.iters)
 
 
+@pytest.mark.parametrize("s", [1, 3])
+def test_batch_member_solve_matches_oracle(rpm, s):
+    """Batched-sweep cells of 48^3 and 96^3 (radix-3 grids): one RPM solve
+    each, mean stress against the FP64 oracle at a tight tolerance."""
+    cell = ms.cell_batch_member(s)
+    l1, m1 = ms.lame(5.0, 0.3)        # moderate contrast so the oracle finishes quickly
+    cell = ms.Cell(phase=cell.phase, lam=np.array([cell.lam[0], l1]), mu=np.array([cell.mu[0], m1]),
+                   lam0=0.5 * (cell.lam[0] + l1), mu0=0.5 * (cell.mu[0] + m1))
+    prob = o.Problem.from_cell(cell)
+    E = ms.unit_strain(5)
+    ref = o.rpm_solve(prob, E, o.Options(tol=1e-10, p_max=10))
+    with rpm.Context(cell, rpm.rpm_default_options(tol=1e-6, p_max=10)) as ctx:
+        st, info = ctx.solve(E)
+    assert info["converged"]
+    d = np.max(np.abs(np.array(info["mean_stress"]) - ref.mean_stress))
+    assert d < CEFF_TOL * np.max(np.abs(ref.mean_stress)), d
+
+
 def test_effective_stiffness_sphere16(rpm):
     cell = ms.cell_sphere32(16)
     prob = o.Problem.from_cell(cell)
