@@ -74,7 +74,15 @@ typedef struct {
   double diverge_factor; /* RPM_ERR_DIVERGED when residual > factor * initial, 1e10 */
   double max_device_gb;  /* refuse contexts needing more device memory; 0 = no cap */
   int profile;           /* 1: time Gamma0 applications and projections with CUDA events */
+  int scheme;            /* RPM_SCHEME_BASIC (Eq. 3.9, default) or RPM_SCHEME_POLARIZATION */
+  double alpha, beta;    /* Algorithm 3 parameters (alpha = beta = 2: Accelerated scheme) */
 } rpm_options;
+
+/* Fixed-point map wrapped by the solver.  BASIC: Eq. 3.9 (Algorithm 1).
+ * POLARIZATION: Algorithm 3 (Section 5.5), read with s_b = alpha sigma -
+ * beta C0:eps (the printed plus sign does not keep the solution a fixed
+ * point); alpha = beta = 2 is the Accelerated scheme. */
+enum { RPM_SCHEME_BASIC = 0, RPM_SCHEME_POLARIZATION = 1 };
 
 typedef struct {
   int iters;           /* fixed-point steps taken */

@@ -318,6 +318,58 @@ cudaError_t launch_axpby(float* out, float a, const float* x, float b, const flo
   return cudaGetLastError();
 }
 
+// eps_next = (C + C0)^-1 : (s_a + C0 : eps_b), Algorithm 3, per voxel; the
+// inverse of an isotropic stiffness (lam_s, mu_s) maps t to
+// (t - lam_s / (3 lam_s + 2 mu_s) tr(t) I) / (2 mu_s).
+__global__ void __launch_bounds__(kRedThreads) k_pol_post(const float4* __restrict__ eps,
+                                                          const float4* __restrict__ epsb,
+                                                          const uchar4* __restrict__ phase,
+                                                          const float4* __restrict__ post,
+                                                          float lam0, float mu0,
+                                                          float4* __restrict__ out, long long n4) {
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n4;
+       q += (long long)gridDim.x * blockDim.x) {
+    const uchar4 ph = phase[q];
+    const float4 pm[4] = {post[ph.x], post[ph.y], post[ph.z], post[ph.w]};
+    float e[6][4], b[6][4];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const float4 u = eps[c * n4 + q], v = epsb[c * n4 + q];
+      e[c][0] = u.x; e[c][1] = u.y; e[c][2] = u.z; e[c][3] = u.w;
+      b[c][0] = v.x; b[c][1] = v.y; b[c][2] = v.z; b[c][3] = v.w;
+    }
+    float o[6][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float tre = e[0][k] + e[1][k] + e[2][k];
+      const float trb = b[0][k] + b[1][k] + b[2][k];
+      float t[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) t[c] = 2.f * pm[k].y * e[c][k] + 2.f * mu0 * b[c][k];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) t[c] += pm[k].x * tre + lam0 * trb;
+      const float trt = t[0] + t[1] + t[2];
+      const float lam_s = pm[k].z, mu_s = pm[k].w;
+      const float sh = lam_s / (3.f * lam_s + 2.f * mu_s) * trt;
+      const float inv2mu = 0.5f / mu_s;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) o[c][k] = (t[c] - (c < 3 ? sh : 0.f)) * inv2mu;
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) out[c * n4 + q] = make_float4(o[c][0], o[c][1], o[c][2], o[c][3]);
+  }
+}
+
+cudaError_t launch_polarization_post(const GridDev& g, const float4* post, const float* eps,
+                                     const float* eps_b, float* out, cudaStream_t st) {
+  const long long n4 = g.n / 4;
+  k_pol_post<<<stream_blocks(n4), kRedThreads, 0, st>>>(
+      reinterpret_cast<const float4*>(eps), reinterpret_cast<const float4*>(eps_b),
+      reinterpret_cast<const uchar4*>(g.phase), post, g.lam0, g.mu0,
+      reinterpret_cast<float4*>(out), n4);
+  return cudaGetLastError();
+}
+
 __global__ void k_fill(float4* f, float e0, float e1, float e2, float e3, float e4, float e5,
                        long long n4) {
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < 6 * n4;

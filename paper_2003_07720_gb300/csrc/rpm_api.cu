@@ -43,13 +43,16 @@ struct rpm_ctx {
   std::vector<rpm_iso> phases;
   rpm_iso c0{};
   GridDev g{};
+  GridDev gb{};                      // g with the Algorithm 3 pre-step table (s_b)
+  float2* dmat_b = nullptr;          // per phase (alpha lam - beta lam0, alpha mu - beta mu0)
+  float4* post = nullptr;            // per phase (lam_a, mu_a, lam_s, mu_s) of Algorithm 3
   long long n = 0;
   size_t fsz = 0;                    // floats per field (6 n)
   size_t fst = 0;                    // stride between internal fields (6 n + pad)
   char* tables = nullptr;
   uint8_t* phase = nullptr;
   float2* spec = nullptr;
-  float* fields = nullptr;           // eps[2], xi[3], D[2]
+  float* fields = nullptr;           // eps[2], xi[3], D[2], eps_b
   float* Z = nullptr;
   float* W = nullptr;
   double* partials = nullptr;
@@ -97,7 +100,29 @@ void build_twiddles(int L, std::vector<float2>& out) {
 
 bool valid_options(const rpm_options& o) {
   return o.n_max >= 1 && o.p_max >= 0 && o.p_max <= kPCap && o.max_iters >= 0 && o.tol >= 0 &&
-         o.t_ratio >= 0 && o.nyquist == RPM_NYQ_ZERO_MIXED && o.diverge_factor > 0;
+         o.t_ratio >= 0 && o.nyquist == RPM_NYQ_ZERO_MIXED && o.diverge_factor > 0 &&
+         (o.scheme == RPM_SCHEME_BASIC || o.scheme == RPM_SCHEME_POLARIZATION) &&
+         std::isfinite(o.alpha) && std::isfinite(o.beta);
+}
+
+// Algorithm 3 tables for the current options: s_b = alpha C:eps - beta C0:eps
+// (isotropic per phase) and the post-step moduli.
+cudaError_t upload_scheme_tables(rpm_ctx* c) {
+  std::vector<float2> db(256, make_float2(0.f, 0.f));
+  std::vector<float4> pt(256, make_float4(0.f, 0.f, 1.f, 1.f));
+  const double a = c->opt.alpha, b = c->opt.beta, l0 = c->c0.lambda, m0 = c->c0.mu;
+  for (size_t i = 0; i < c->phases.size(); ++i) {
+    const double l = c->phases[i].lambda, m = c->phases[i].mu;
+    db[i] = make_float2((float)(a * l - b * l0), (float)(a * m - b * m0));
+    pt[i] = make_float4((float)(l + (1.0 - b) * l0), (float)(m + (1.0 - b) * m0), (float)(l + l0),
+                        (float)(m + m0));
+  }
+  cudaError_t e = cudaMemcpyAsync(c->dmat_b, db.data(), 256 * sizeof(float2),
+                                  cudaMemcpyHostToDevice, c->st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(c->post, pt.data(), 256 * sizeof(float4), cudaMemcpyHostToDevice, c->st);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(c->st);
 }
 
 // Gauss-Jordan inverse with partial pivoting (p <= 32), float64.
@@ -171,6 +196,22 @@ struct Ops {
     done(m);
     return ok;
   }
+  // the solver's fixed-point map F (linear: F_u, i.e. E = 0)
+  bool fmap(const float* in, float* out, const double* E, bool linear) {
+    if (c->opt.scheme == RPM_SCHEME_BASIC) return gamma(in, out, E, linear ? GM_LINEAR : GM_FULL_MAP);
+    const size_t m = mark(0);
+    c->launches += gamma_launches(c->g.nx, c->g.ny) + 1;
+    float* eb = c->fields + 7 * c->fst;
+    double Eb[6] = {0, 0, 0, 0, 0, 0};
+    if (!linear)
+      for (int k = 0; k < 6; ++k) Eb[k] = c->opt.beta * E[k];
+    bool ok = ck(c, launch_apply_gamma(c->gb, in, eb, c->spec, Eb, linear ? GM_LINEAR : GM_FULL_MAP,
+                                       c->st),
+                 "apply_gamma") &&
+              ck(c, launch_polarization_post(c->g, c->post, in, eb, out, c->st), "post");
+    done(m);
+    return ok;
+  }
   // sums[0..K] <- dots of x against Y (see launch_dots)
   bool dots(const float* x, const float* xm, const float* Y, int K, double* sums) {
     const size_t m = mark(1);
@@ -217,6 +258,9 @@ void rpm_default_options(rpm_options* o) {
   o->diverge_factor = 1e10;
   o->max_device_gb = 0.0;
   o->profile = 0;
+  o->scheme = RPM_SCHEME_BASIC;
+  o->alpha = 2.0;
+  o->beta = 2.0;
 }
 
 int rpm_grid_supported(int nx, int ny, int nz) { return grid_supported(nx, ny, nz) ? 1 : 0; }
@@ -274,10 +318,10 @@ rpm_status rpm_set_options(rpm_ctx* c, const rpm_options* o) {
   if (!c || !o) return fail(c, RPM_ERR_INVALID_ARG, "null argument");
   if (!valid_options(*o) || o->p_max > c->p_cap)
     return fail(c, RPM_ERR_INVALID_ARG, "invalid options (p_max above the creation value?)");
-  const int nyq_old = c->opt.nyquist;
   c->opt = *o;
   c->g.nyquist = o->nyquist;
-  (void)nyq_old;
+  c->gb.nyquist = o->nyquist;
+  if (!ck(c, upload_scheme_tables(c), "scheme tables")) return RPM_ERR_CUDA;
   return RPM_OK;
 }
 
@@ -355,11 +399,13 @@ rpm_status rpm_create(const rpm_grid* grid, const uint8_t* phase, int phase_on_d
   const size_t o_fy = off; off = align_up(off + fy.size() * 8, 256);
   const size_t o_dm = off; off = align_up(off + 256 * 8, 256);
   const size_t o_cm = off; off = align_up(off + 256 * 8, 256);
+  const size_t o_db = off; off = align_up(off + 256 * 8, 256);
+  const size_t o_pt = off; off = align_up(off + 256 * 16, 256);
   const size_t tab_bytes = off;
   c->nblk = std::max(dots_blocks_for(c->n), stress_blocks_for(c->n));
   const size_t fbytes = c->fst * sizeof(float);
   const size_t spec_bytes = (size_t)6 * nz * g.plane * sizeof(float2);
-  const size_t need = tab_bytes + align_up((size_t)c->n, 256) + spec_bytes + 7 * fbytes +
+  const size_t need = tab_bytes + align_up((size_t)c->n, 256) + spec_bytes + 8 * fbytes +
                       2 * (size_t)c->p_cap * fbytes + (size_t)(kPCap + 1) * c->nblk * 8 +
                       kSmall * 8;
   if (o.max_device_gb > 0 && (double)need > o.max_device_gb * 1e9) {
@@ -376,7 +422,7 @@ rpm_status rpm_create(const rpm_grid* grid, const uint8_t* phase, int phase_on_d
   if ((e = alloc((void**)&c->tables, tab_bytes)) != cudaSuccess ||
       (e = alloc((void**)&c->phase, align_up((size_t)c->n, 256))) != cudaSuccess ||
       (e = alloc((void**)&c->spec, spec_bytes)) != cudaSuccess ||
-      (e = alloc((void**)&c->fields, 7 * fbytes)) != cudaSuccess ||
+      (e = alloc((void**)&c->fields, 8 * fbytes)) != cudaSuccess ||
       (e = alloc((void**)&c->Z, (size_t)c->p_cap * fbytes)) != cudaSuccess ||
       (e = alloc((void**)&c->W, (size_t)c->p_cap * fbytes)) != cudaSuccess ||
       (e = alloc((void**)&c->partials, (size_t)(kPCap + 1) * c->nblk * 8)) != cudaSuccess ||
@@ -421,6 +467,14 @@ rpm_status rpm_create(const rpm_grid* grid, const uint8_t* phase, int phase_on_d
   g.dmat = (const float2*)(t + o_dm);
   g.cmat = (const float2*)(t + o_cm);
   g.phase = c->phase;
+  c->dmat_b = (float2*)(t + o_db);
+  c->post = (float4*)(t + o_pt);
+  c->gb = g;
+  c->gb.dmat = c->dmat_b;
+  if (!ck(c, upload_scheme_tables(c), "scheme tables")) {
+    rpm_destroy(c);
+    return RPM_ERR_CUDA;
+  }
   rpm_status s = rpm_set_phase(c, phase, phase_on_device);
   if (s == RPM_OK && cudaStreamSynchronize(c->st) != cudaSuccess) s = RPM_ERR_CUDA;
   if (s != RPM_OK) {
@@ -489,7 +543,7 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
     return RPM_ERR_CUDA;
   }
   int cur = 0, hist = 1, it = 0, nu = 0, nF = 0;
-  if (!ops.gamma(eps_cur, xi[0], E, GM_FULL_MAP)) return RPM_ERR_CUDA;
+  if (!ops.fmap(eps_cur, xi[0], E, false)) return RPM_ERR_CUDA;
   nF = 1;
 
   // residual, zeta = Z^T xi and the Newton correction for the current pair (eps, xi)
@@ -555,7 +609,7 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
       float* zp = c->Z + (size_t)c->p * F;
       if (!ck(c, (++c->launches, launch_axpby)(zp, (float)(1.0 / nu_), u, 0.f, nullptr, c->n, c->st), "axpby"))
         return false;
-      if (!ops.gamma(zp, c->W + (size_t)c->p * F, nullptr, GM_LINEAR)) return false;
+      if (!ops.fmap(zp, c->W + (size_t)c->p * F, nullptr, true)) return false;
       ++nF;
       ++c->p;
     }
@@ -623,7 +677,7 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
       std::swap(zcur, znext);
     }
     const int nxt = (cur + 1) % 3;
-    if (!ops.gamma(eps_next, xi[nxt], E, GM_FULL_MAP)) return RPM_ERR_CUDA;
+    if (!ops.fmap(eps_next, xi[nxt], E, false)) return RPM_ERR_CUDA;
     ++nF;
     ++it;
     ++nu;

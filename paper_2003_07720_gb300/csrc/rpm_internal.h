@@ -64,6 +64,10 @@ cudaError_t launch_axpby(float* out, float a, const float* x, float b, const flo
 cudaError_t launch_stress(const GridDev& g, const float* eps, float* sig /*nullable*/,
                           double* partials, int nblk, cudaStream_t st);
 cudaError_t launch_fill(float* f, const double E[6], long long n, cudaStream_t st);
+// Algorithm 3's last step: out = (C + C0)^-1 : (s_a(eps) + C0 : eps_b), with per-phase
+// table post[r] = (lam_a, mu_a, lam_s, mu_s); s_a = lam_a tr(eps) I + 2 mu_a eps.
+cudaError_t launch_polarization_post(const GridDev& g, const float4* post, const float* eps,
+                                     const float* eps_b, float* out, cudaStream_t st);
 cudaError_t launch_newton(const double* sums, int p, const double* M, const double* z, double* c,
                           double* znext, double* res_out, double inv_norm, cudaStream_t st);
 

@@ -27,6 +27,9 @@ RPM_ERR_TIMEOUT = 7
 
 RPM_NYQ_ZERO_MIXED = 0
 
+RPM_SCHEME_BASIC = 0
+RPM_SCHEME_POLARIZATION = 1
+
 RPM_GAMMA_FULL_MAP = 0
 RPM_GAMMA_LINEAR = 1
 RPM_GAMMA_RAW_TAU = 2
@@ -45,7 +48,8 @@ class rpm_options(ctypes.Structure):
     _fields_ = [("n_max", ctypes.c_int), ("p_max", ctypes.c_int), ("max_iters", ctypes.c_int),
                 ("tol", ctypes.c_double), ("t_ratio", ctypes.c_double),
                 ("nyquist", ctypes.c_int), ("diverge_factor", ctypes.c_double),
-                ("max_device_gb", ctypes.c_double), ("profile", ctypes.c_int)]
+                ("max_device_gb", ctypes.c_double), ("profile", ctypes.c_int),
+                ("scheme", ctypes.c_int), ("alpha", ctypes.c_double), ("beta", ctypes.c_double)]
 
 
 class rpm_solve_info(ctypes.Structure):

@@ -187,3 +187,46 @@ def test_failure_paths(rpm):
     with pytest.raises(rpm.RpmError) as ei:
         rpm.Context(cell, rpm.rpm_default_options(max_device_gb=1e-6))
     assert ei.value.status == rpm.RPM_ERR_OOM
+
+
+@pytest.mark.parametrize("alpha,beta", [(2.0, 2.0), (1.5, 1.0)])
+def test_polarization_map_matches_oracle(rpm, alpha, beta):
+    """One application of Algorithm 3 on the GPU (warm start x, one step)
+    against the oracle's map, element by element."""
+    cell = ms.cell_sphere32(32)
+    prob = o.Problem.from_cell(cell)
+    E = ms.unit_strain(0)
+    rng = np.random.Generator(np.random.PCG64(4))
+    x = (E.reshape(6, 1, 1, 1) + 0.2 * rng.standard_normal((6,) + cell.shape)).astype(np.float32)
+    out = torch.empty((6,) + cell.shape, device="cuda")
+    opts = rpm.rpm_default_options(scheme=rpm.RPM_SCHEME_POLARIZATION, alpha=alpha, beta=beta,
+                                   max_iters=1, tol=0.0, p_max=0)
+    with rpm.Context(cell, opts) as ctx:
+        st, info = ctx.solve(E, eps0=torch.from_numpy(x).cuda(), eps_out=out, raise_on_failure=False)
+    assert st == rpm.RPM_ERR_NOT_CONVERGED and info["iters"] == 1
+    ref = o.apply_F_polarization(prob, x.astype(np.float64), E, alpha, beta)
+    got = out.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-5
+
+
+def test_rpm_accelerated_solve_matches_oracle(rpm):
+    """RPM wrapped around the Accelerated scheme (Section 5.5) on the 32^3
+    sphere cell with C0 at the geometric mean of the phase moduli."""
+    cell = ms.cell_sphere32(32)
+    g = np.sqrt(10.0)
+    l0, m0 = ms.lame(g, 0.3)
+    cell = ms.Cell(phase=cell.phase, lam=cell.lam, mu=cell.mu, lam0=l0, mu0=m0)
+    prob = o.Problem.from_cell(cell)
+    E = ms.unit_strain(3)
+    ref = o.rpm_solve(prob, E, o.Options(tol=1e-11, p_max=10, scheme="polarization"))
+    r6 = o.rpm_solve(prob, E, o.Options(tol=1e-6, p_max=10, scheme="polarization"))
+    eps = torch.empty((6,) + cell.shape, device="cuda")
+    opts = rpm.rpm_default_options(scheme=rpm.RPM_SCHEME_POLARIZATION, tol=1e-6, p_max=10)
+    with rpm.Context(cell, opts) as ctx:
+        st, info = ctx.solve(E, eps_out=eps)
+    assert info["converged"]
+    assert abs(info["iters"] - r6.iters) <= max(3, r6.iters // 5)
+    d = np.max(np.abs(np.array(info["mean_stress"]) - ref.mean_stress))
+    assert d < CEFF_TOL * np.max(np.abs(ref.mean_stress))
+    e = eps.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(e - ref.eps) / np.linalg.norm(ref.eps) < FIELD_TOL

@@ -445,3 +445,39 @@ def test_hashin_shtrikman_random_spheres():
     assert Kl * 0.99 <= K <= Ku * 1.01
     assert Gl * 0.99 <= G <= Gu * 1.01
     assert K > Kl and G > Gl
+
+
+# ----------------------------------------------------------------------------
+# Algorithm 3 (polarization / Accelerated scheme)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("alpha,beta", [(2.0, 2.0), (1.0, 1.0), (1.5, 0.7)])
+def test_polarization_homogeneous_closed_form(alpha, beta):
+    """C = c C0 uniform (same nu), eps = E + e with e compatible, zero mean:
+    F(eps) = E + ((1 - alpha) c + 1) / (c + 1) e  (for alpha = 2 the
+    Eyre-Milton contraction (1 - c)/(1 + c), derived independently from the
+    Cayley transform of C0^-1 C and the reflection 2 Gamma0 C0 - I)."""
+    shape = (6, 8, 8)
+    c = 4.0
+    l0, m0 = ms.lame(1.5, 0.3)
+    p = o.Problem(phase=np.zeros(shape, np.uint8), lam=np.array([c * l0]), mu=np.array([c * m0]),
+                  lam0=l0, mu0=m0)
+    E = _rng(8).standard_normal(6)
+    e = _compatible_field(shape, seed=13, amp=0.2)
+    got = o.apply_F_polarization(p, E.reshape(6, 1, 1, 1) + e, E, alpha, beta)
+    fac = ((1 - alpha) * c + 1) / (c + 1)
+    assert np.max(np.abs(got - (E.reshape(6, 1, 1, 1) + fac * e))) < 1e-12
+
+
+@pytest.mark.parametrize("alpha,beta", [(2.0, 2.0), (1.0, 1.0), (1.5, 1.5)])
+def test_polarization_solution_is_fixed_point_and_solvers_converge(tiny, alpha, beta):
+    """The cell-problem solution (dense solve of the basic map) is a fixed
+    point of Algorithm 3, and Algorithm 3 alone and wrapped by RPM converge to
+    it."""
+    p, L = tiny
+    E = ms.unit_strain(1)
+    ref = np.linalg.solve(np.eye(L.shape[0]) - L, o.uniform(E, p.shape).ravel()).reshape((6,) + p.shape)
+    assert np.max(np.abs(o.apply_F_polarization(p, ref, E, alpha, beta) - ref)) < 1e-12
+    kw = dict(scheme="polarization", alpha=alpha, beta=beta, tol=1e-11, max_iters=4000)
+    for r in (o.basic_solve(p, E, o.Options(**kw)), o.rpm_solve(p, E, o.Options(p_max=20, **kw))):
+        assert r.converged
+        assert np.max(np.abs(r.eps - ref)) < 1e-8
