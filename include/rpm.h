@@ -76,6 +76,16 @@ typedef struct {
   int profile;           /* 1: time Gamma0 applications and projections with CUDA events */
   int scheme;            /* RPM_SCHEME_BASIC (Eq. 3.9, default) or RPM_SCHEME_POLARIZATION */
   double alpha, beta;    /* Algorithm 3 parameters (alpha = beta = 2: Accelerated scheme) */
+  /* Warm start (cold start when warm_tol <= 0, the default): before the
+   * solve proper, iterate Algorithm 3 (alpha, beta as above, no basis) with
+   * the reference medium at the geometric mean (lambda_min lambda_max)^1/2,
+   * (mu_min mu_max)^1/2 of the phases scaled by warm_c0_scale, until its own
+   * increment is <= warm_tol (at most warm_max_iters steps); then run the
+   * configured scheme from that strain to tol.  Only the stopping test of the
+   * second stage decides convergence. */
+  double warm_tol;
+  double warm_c0_scale;  /* default 1 */
+  int warm_max_iters;    /* default 2000 */
 } rpm_options;
 
 /* Fixed-point map wrapped by the solver.  BASIC: Eq. 3.9 (Algorithm 1).
@@ -98,6 +108,8 @@ typedef struct {
   float proj_ms;       /* with opt.profile: summed time of the projection/combine kernels */
   long long launches;  /* CUDA kernels launched by the solve */
   double proj_bytes;   /* algorithmic bytes moved by the projection/combine kernels */
+  int warm_iters;      /* steps of the warm-start stage (0: cold start) */
+  double warm_residual;/* increment of the warm-start stage when it stopped */
 } rpm_solve_info;
 
 /* Fill `opt` with the defaults listed above. */

@@ -236,10 +236,11 @@ __host__ __device__ inline int freq_of_rt(int N, int s) {
 // index n2*N1 + k1 (forward sign).  Forward: natural -> slot order; inverse:
 // slot order -> natural.  Unnormalised.  Every thread of the block must call
 // it; it ends with __syncthreads().
-template <int N, bool INV, int NLINES>
-__device__ __forceinline__ void smem_fft(float2* buf, int lstride, int estride, const float2* tw) {
+template <int N, bool INV, int NLINES, int LSTRIDE, int ESTRIDE>
+__device__ __forceinline__ void smem_fft(float2* buf, const float2* tw) {
   constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
-  constexpr int nlines = NLINES;       // compile-time: task index splits are mul-shifts
+  // compile-time shape: task splits are mul-shifts, element offsets immediates
+  constexpr int nlines = NLINES, lstride = LSTRIDE, estride = ESTRIDE;
   if (N == 1) return;
   if (!INV) {
     for (int t = threadIdx.x; t < nlines * N2; t += blockDim.x) {

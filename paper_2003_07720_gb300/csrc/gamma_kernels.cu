@@ -51,9 +51,13 @@ __device__ __forceinline__ float2 c2r_pre(float2 a, float2 b, float2 w) {
   return make_float2(s.x - u.y, s.y + u.x);
 }
 
+// Block size of the plane passes and the blocks per SM the register budget targets.
+constexpr int kPlaneThreads = 256;
+constexpr int kPlaneMinBlocks = 3;
+
 template <int NX, int NY>
-__global__ void __launch_bounds__(kThreads) k_pass_a(GridDev g, const float* __restrict__ in,
-                                                     float2* __restrict__ spec, int mode) {
+__global__ void __launch_bounds__(kPlaneThreads, kPlaneMinBlocks)
+    k_pass_a(GridDev g, const float* __restrict__ in, float2* __restrict__ spec, int mode) {
   using C = PlaneCfg<NX, NY>;
   extern __shared__ float2 sm[];
   float2* P = sm;
@@ -75,12 +79,12 @@ __global__ void __launch_bounds__(kThreads) k_pass_a(GridDev g, const float* __r
   // Loads are issued in groups of U per thread before any use, so each thread
   // keeps several independent requests in flight (the plane is streamed once).
   constexpr int TOT = NY * C::NXH, U = 4;
-  for (int base = threadIdx.x; base < TOT; base += U * kThreads) {
+  for (int base = threadIdx.x; base < TOT; base += U * kPlaneThreads) {
     float2 a[U], b[U], d[U];
     uchar2 ph[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int idx = base + u * kThreads;
+      const int idx = base + u * kPlaneThreads;
       if (idx < TOT) {
         const size_t v = z2 + idx;
         if (mode == GM_RAW_TAU || c >= 3) {
@@ -95,7 +99,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_a(GridDev g, const float* __r
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int idx = base + u * kThreads;
+      const int idx = base + u * kPlaneThreads;
       if (idx < TOT) {
         const int y = idx / C::NXH, h = idx - y * C::NXH;
         float2 t;
@@ -116,7 +120,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_a(GridDev g, const float* __r
     }
   }
   __syncthreads();
-  smem_fft<C::NXH, false, NY>(P, 1, C::NYP, twx);
+  smem_fft<C::NXH, false, NY, 1, C::NYP>(P, twx);
   for (int t = threadIdx.x; t < NY * (C::NXH / 2 + 1); t += blockDim.x) {
     const int y = t % NY, k = t / NY;
     if (k == 0) {
@@ -132,7 +136,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_a(GridDev g, const float* __r
     }
   }
   __syncthreads();
-  smem_fft<NY, false, C::SX>(P, C::NYP, 1, twy);
+  smem_fft<NY, false, C::SX, C::NYP, 1>(P, twy);
   float2* out = spec + ((size_t)c * g.nz + z) * g.plane;
   for (int idx = threadIdx.x; idx < NY * C::SX; idx += blockDim.x) {
     const int sy = idx / C::SX, sx = idx - sy * C::SX;
@@ -141,8 +145,8 @@ __global__ void __launch_bounds__(kThreads) k_pass_a(GridDev g, const float* __r
 }
 
 template <int NX, int NY>
-__global__ void __launch_bounds__(kThreads) k_pass_c(GridDev g, const float2* __restrict__ spec,
-                                                     float* __restrict__ outp, float scale) {
+__global__ void __launch_bounds__(kPlaneThreads, kPlaneMinBlocks)
+    k_pass_c(GridDev g, const float2* __restrict__ spec, float* __restrict__ outp, float scale) {
   using C = PlaneCfg<NX, NY>;
   extern __shared__ float2 sm[];
   float2* P = sm;
@@ -156,16 +160,16 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(GridDev g, const float2* __
   const float2* src = spec + ((size_t)c * g.nz + z) * g.plane;
   {
     constexpr int TOT = NY * C::SX, U = 8;
-    for (int base = threadIdx.x; base < TOT; base += U * kThreads) {
+    for (int base = threadIdx.x; base < TOT; base += U * kPlaneThreads) {
       float2 v[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int idx = base + u * kThreads;
+        const int idx = base + u * kPlaneThreads;
         if (idx < TOT) v[u] = src[idx];
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int idx = base + u * kThreads;
+        const int idx = base + u * kPlaneThreads;
         if (idx < TOT) {
           const int sy = idx / C::SX, sx = idx - sy * C::SX;
           P[sx * C::NYP + sy] = v[u];
@@ -174,7 +178,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(GridDev g, const float2* __
     }
   }
   __syncthreads();
-  smem_fft<NY, true, C::SX>(P, C::NYP, 1, twy);
+  smem_fft<NY, true, C::SX, C::NYP, 1>(P, twy);
   for (int t = threadIdx.x; t < NY * (C::NXH / 2 + 1); t += blockDim.x) {
     const int y = t % NY, k = t / NY;
     if (k == 0) {
@@ -188,7 +192,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(GridDev g, const float2* __
     }
   }
   __syncthreads();
-  smem_fft<C::NXH, true, NY>(P, 1, C::NYP, twx);
+  smem_fft<C::NXH, true, NY, 1, C::NYP>(P, twx);
   const size_t n2 = (size_t)g.n / 2;
   float2* out2 = reinterpret_cast<float2*>(outp) + c * n2 + (size_t)z * NY * C::NXH;
   for (int idx = threadIdx.x; idx < NY * C::NXH; idx += blockDim.x) {
@@ -244,9 +248,22 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(GridDev g, float2* __restri
   extern __shared__ float2 sm[];
   float2* B = sm;
   float2* twz = B + 6 * T * NZP;
+  __shared__ float4 pen[T];          // per pencil: (xi_x, xi_y, has-Nyquist, non-zero count)
   for (int i = threadIdx.x; i < NZ; i += blockDim.x) twz[i] = g.tw_z[i];
   const int m0 = blockIdx.x * T;
   const int plane = g.plane;
+  if (threadIdx.x < T) {
+    const int m = m0 + threadIdx.x;
+    float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (m < plane) {
+      const int sxn = g.nxh + 1;
+      const int sy = m / sxn, sx = m - sy * sxn;
+      const int2 fx = g.fx[sx], fy = g.fy[sy];
+      q = make_float4(fx.x * g.inv_lx, fy.x * g.inv_ly, (float)(fx.y | fy.y),
+                      (float)((fx.x != 0) + (fy.x != 0)));
+    }
+    pen[threadIdx.x] = q;
+  }
   {
     constexpr int TOT = 6 * NZ * T, U = 8;
     for (int base = threadIdx.x; base < TOT; base += U * kThreads) {
@@ -270,30 +287,27 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(GridDev g, float2* __restri
     }
   }
   __syncthreads();
-  smem_fft<NZ, false, 6 * T>(B, NZP, 1, twz);
-  const int sxn = g.nxh + 1;
+  smem_fft<NZ, false, 6 * T, NZP, 1>(B, twz);
   for (int idx = threadIdx.x; idx < T * NZ; idx += blockDim.x) {
     const int sz = idx % NZ, t = idx / NZ;
-    const int m = m0 + t;
-    if (m >= plane) continue;
-    const int sy = m / sxn, sx = m - sy * sxn;
-    const int2 fx = g.fx[sx], fy = g.fy[sy];
+    if (m0 + t >= plane) continue;
+    const float4 q = pen[t];
     const int kz = freq_of<NZ>(sz);
-    int mz = (2 * kz < NZ) ? kz : kz - NZ;
+    const int mz = (2 * kz < NZ) ? kz : kz - NZ;
     const bool nyqz = (NZ % 2 == 0) && NZ > 1 && (2 * kz == NZ);
     float2 tv[6];
 #pragma unroll
     for (int c = 0; c < 6; ++c) tv[c] = B[(c * T + t) * NZP + sz];
-    const int nnz = (fx.x != 0) + (fy.x != 0) + (mz != 0);
+    const int nnz = (int)q.w + (mz != 0);
     if (nnz == 0) {
 #pragma unroll
       for (int c = 0; c < 6; ++c)
         tv[c] = make_float2(mode == GM_FULL_MAP ? ga.En[c] : 0.f, 0.f);
-    } else if (g.nyquist == 0 && nnz >= 2 && (fx.y || fy.y || nyqz)) {
+    } else if (g.nyquist == 0 && nnz >= 2 && (q.z != 0.f || nyqz)) {
 #pragma unroll
       for (int c = 0; c < 6; ++c) tv[c] = make_float2(0.f, 0.f);
     } else {
-      const float x1 = fx.x * g.inv_lx, x2 = fy.x * g.inv_ly, x3 = mz * g.inv_lz;
+      const float x1 = q.x, x2 = q.y, x3 = mz * g.inv_lz;
       const float inv = 1.f / sqrtf(x1 * x1 + x2 * x2 + x3 * x3);
       green_apply(tv, x1 * inv, x2 * inv, x3 * inv, ga.a, ga.inv_mu0);
     }
@@ -301,7 +315,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(GridDev g, float2* __restri
     for (int c = 0; c < 6; ++c) B[(c * T + t) * NZP + sz] = tv[c];
   }
   __syncthreads();
-  smem_fft<NZ, true, 6 * T>(B, NZP, 1, twz);
+  smem_fft<NZ, true, 6 * T, NZP, 1>(B, twz);
   for (int idx = threadIdx.x; idx < 6 * NZ * T; idx += blockDim.x) {
     const int t = idx % T, r = idx / T, z = r % NZ, c = r / NZ;
     const int m = m0 + t;
@@ -360,7 +374,7 @@ __global__ void __launch_bounds__(kThreads) k_rows_fwd(GridDev g, const float* _
     P[h * kRowsP + r] = t;
   }
   __syncthreads();
-  smem_fft<NXH, false, kRows>(P, 1, kRowsP, twx);
+  smem_fft<NXH, false, kRows, 1, kRowsP>(P, twx);
   for (int t = threadIdx.x; t < kRows * (NXH / 2 + 1); t += blockDim.x) {
     const int r = t % kRows, k = t / kRows;
     if (k == 0) {
@@ -414,7 +428,7 @@ __global__ void __launch_bounds__(kThreads) k_rows_inv(GridDev g, const float2* 
     }
   }
   __syncthreads();
-  smem_fft<NXH, true, kRows>(P, 1, kRowsP, twx);
+  smem_fft<NXH, true, kRows, 1, kRowsP>(P, twx);
   const size_t n2 = (size_t)g.n / 2;
   float2* out2 = reinterpret_cast<float2*>(outp) + c * n2 + ((size_t)z * ny + y0) * NXH;
   for (int idx = threadIdx.x; idx < kRows * NXH; idx += blockDim.x) {
@@ -446,7 +460,7 @@ __global__ void __launch_bounds__(kThreads) k_ypencil(GridDev g, float2* __restr
     B[t * NYP + y] = (sx0 + t < SX) ? pl[(size_t)y * SX + sx0 + t] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  smem_fft<NY, INV, TY>(B, NYP, 1, twy);
+  smem_fft<NY, INV, TY, NYP, 1>(B, twy);
   for (int idx = threadIdx.x; idx < TY * NY; idx += blockDim.x) {
     const int t = idx % TY, y = idx / TY;
     if (sx0 + t < SX) pl[(size_t)y * SX + sx0 + t] = B[t * NYP + y];
@@ -471,12 +485,12 @@ static cudaError_t launch_plane_passes(const GridDev& g, const float* in, float*
     const size_t smem = (size_t)(C::PLANE_F2 + C::TAB_F2 + 256) * sizeof(float2);
     cudaError_t e = set_smem(k_pass_a<NX, NX>, smem);
     if (e != cudaSuccess) return e;
-    k_pass_a<NX, NX><<<grid, kThreads, smem, st>>>(g, in, spec, mode);
+    k_pass_a<NX, NX><<<grid, kPlaneThreads, smem, st>>>(g, in, spec, mode);
   } else {
     const size_t smem = (size_t)(C::PLANE_F2 + C::TAB_F2) * sizeof(float2);
     cudaError_t e = set_smem(k_pass_c<NX, NX>, smem);
     if (e != cudaSuccess) return e;
-    k_pass_c<NX, NX><<<grid, kThreads, smem, st>>>(g, spec, out, 1.0f / (float)g.n);
+    k_pass_c<NX, NX><<<grid, kPlaneThreads, smem, st>>>(g, spec, out, 1.0f / (float)g.n);
   }
   return cudaGetLastError();
 }

@@ -27,7 +27,8 @@ constexpr int kSums = 0;              // 1 + kPCap reduced sums
 constexpr int kZa = kSums + kPCap + 8;   // reduced coordinates z (two buffers)
 constexpr int kZb = kZa + kPCap;
 constexpr int kC = kZb + kPCap;       // Newton correction c
-constexpr int kRes = kC + kPCap;      // residual
+constexpr int kRes = kC + kPCap;      // residuals (up to kBatch)
+constexpr int kBatch = 4;             // steps between host reads while the basis is empty
 constexpr int kM = kRes + 8;          // (I - H)^-1, kPCap x kPCap
 constexpr int kSmall = kM + kPCap * kPCap;
 
@@ -102,7 +103,30 @@ bool valid_options(const rpm_options& o) {
   return o.n_max >= 1 && o.p_max >= 0 && o.p_max <= kPCap && o.max_iters >= 0 && o.tol >= 0 &&
          o.t_ratio >= 0 && o.nyquist == RPM_NYQ_ZERO_MIXED && o.diverge_factor > 0 &&
          (o.scheme == RPM_SCHEME_BASIC || o.scheme == RPM_SCHEME_POLARIZATION) &&
-         std::isfinite(o.alpha) && std::isfinite(o.beta);
+         std::isfinite(o.alpha) && std::isfinite(o.beta) && std::isfinite(o.warm_tol) &&
+         o.warm_c0_scale > 0 && o.warm_max_iters >= 0;
+}
+
+// Per-phase (lam - lam0, mu - mu0) for the polarization of pass A.
+cudaError_t upload_dmat(rpm_ctx* c) {
+  std::vector<float2> dm(256, make_float2(0.f, 0.f));
+  for (size_t i = 0; i < c->phases.size(); ++i)
+    dm[i] = make_float2((float)(c->phases[i].lambda - c->c0.lambda),
+                        (float)(c->phases[i].mu - c->c0.mu));
+  return cudaMemcpyAsync((void*)c->g.dmat, dm.data(), 256 * sizeof(float2),
+                         cudaMemcpyHostToDevice, c->st);
+}
+
+cudaError_t upload_scheme_tables(rpm_ctx* c);
+
+// Switch the reference medium C0 of the context (tables and Green operator).
+cudaError_t set_reference_medium(rpm_ctx* c, rpm_iso c0) {
+  c->c0 = c0;
+  c->g.lam0 = c->gb.lam0 = (float)c0.lambda;
+  c->g.mu0 = c->gb.mu0 = (float)c0.mu;
+  cudaError_t e = upload_dmat(c);
+  if (e != cudaSuccess) return e;
+  return upload_scheme_tables(c);
 }
 
 // Algorithm 3 tables for the current options: s_b = alpha C:eps - beta C0:eps
@@ -261,6 +285,9 @@ void rpm_default_options(rpm_options* o) {
   o->scheme = RPM_SCHEME_BASIC;
   o->alpha = 2.0;
   o->beta = 2.0;
+  o->warm_tol = 0.0;
+  o->warm_c0_scale = 1.0;
+  o->warm_max_iters = 2000;
 }
 
 int rpm_grid_supported(int nx, int ny, int nz) { return grid_supported(nx, ny, nz) ? 1 : 0; }
@@ -547,6 +574,14 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
   nF = 1;
 
   // residual, zeta = Z^T xi and the Newton correction for the current pair (eps, xi)
+  // residual, zeta and the Newton correction without reading them back (slot k of kRes)
+  auto eval_async = [&](int k) -> bool {
+    if (!ops.dots(xi[cur], eps_cur, c->Z, c->p, ds + kSums)) return false;
+    c->launches += 1;
+    return ck(c, launch_newton(ds + kSums, c->p, ds + kM, ds + zcur, ds + kC, ds + znext,
+                               ds + kRes + k, inv_norm, c->st),
+              "newton");
+  };
   auto eval = [&](double& r) -> bool {
     if (!ops.dots(xi[cur], eps_cur, c->Z, c->p, ds + kSums)) return false;
     c->launches += 1;
@@ -668,24 +703,50 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
       status = RPM_ERR_NOT_CONVERGED;
       break;
     }
-    float* eps_next;
+    // Without a basis the steps need no host decision between them: run up to
+    // kBatch of them back to back and read their residuals once (never past a
+    // basis-growth point or max_iters).  Convergence is tested on the last
+    // iterate of the batch.
+    int batch = 1;
     if (c->p == 0) {
-      eps_next = xi[cur];
-    } else {
-      eps_next = (eps_cur == epsb[0]) ? epsb[1] : epsb[0];
-      if (!ops.combine(eps_next, xi[cur], 1.f, c->Z, c->p, ds + kC, 1.f)) return RPM_ERR_CUDA;
-      std::swap(zcur, znext);
+      batch = kBatch;
+      if (c->p < std::min(o.p_max, c->p_cap)) batch = std::min(batch, o.n_max + 1 - nu);
+      batch = std::max(1, std::min(batch, o.max_iters - it));
     }
-    const int nxt = (cur + 1) % 3;
-    if (!ops.fmap(eps_next, xi[nxt], E, false)) return RPM_ERR_CUDA;
-    ++nF;
-    ++it;
-    ++nu;
-    cur = nxt;
-    hist = std::min(hist + 1, 3);
-    eps_cur = eps_next;
-    if (!eval(r)) return RPM_ERR_CUDA;
-    trace(it, r);
+    for (int b = 0; b < batch; ++b) {
+      float* eps_next;
+      if (c->p == 0) {
+        eps_next = xi[cur];
+      } else {
+        eps_next = (eps_cur == epsb[0]) ? epsb[1] : epsb[0];
+        if (!ops.combine(eps_next, xi[cur], 1.f, c->Z, c->p, ds + kC, 1.f)) return RPM_ERR_CUDA;
+        std::swap(zcur, znext);
+      }
+      const int nxt = (cur + 1) % 3;
+      if (!ops.fmap(eps_next, xi[nxt], E, false)) return RPM_ERR_CUDA;
+      ++nF;
+      ++it;
+      ++nu;
+      cur = nxt;
+      hist = std::min(hist + 1, 3);
+      eps_cur = eps_next;
+      if (batch > 1) {
+        if (!eval_async(b)) return RPM_ERR_CUDA;
+      } else if (!eval(r)) {
+        return RPM_ERR_CUDA;
+      }
+    }
+    if (batch > 1) {
+      if (!ops.read_small(kRes, batch)) return RPM_ERR_CUDA;
+      for (int b = 0; b < batch; ++b) {
+        trace(it - batch + 1 + b, hs[kRes + b]);
+        if (!std::isfinite(hs[kRes + b])) r = hs[kRes + b];
+      }
+      if (std::isfinite(r)) r = hs[kRes + batch - 1];
+      if (!std::isfinite(r)) continue;            // reported as diverged at the loop top
+    } else {
+      trace(it, r);
+    }
     if (std::isfinite(r) && r > o.tol && r <= o.diverge_factor * r0 && nu > o.n_max) {
       if (c->p < std::min(o.p_max, c->p_cap) && hist == 3) {
         const int p_before = c->p;
@@ -748,10 +809,66 @@ rpm_status rpm_solve(rpm_ctx* c, const double E[6], const float* eps0, float* ep
   if (!c || !E) return fail(c, RPM_ERR_INVALID_ARG, "null argument");
   for (int k = 0; k < 6; ++k)
     if (!std::isfinite(E[k])) return fail(c, RPM_ERR_INVALID_ARG, "non-finite E");
-  rpm_status s = solve_impl(c, E, eps0, eps_out, sig_out, out_on_host, info);
+  rpm_solve_info warm{};
+  const float* start = eps0;
+  float ms_warm = 0.f, gms_warm = 0.f, pms_warm = 0.f;
+  long long launches_warm = 0;
+  double pbytes_warm = 0.0;
+  int f_warm = 0;
+  if (c->opt.warm_tol > 0 && !eps0) {
+    // stage 1: Algorithm 3 without basis, C0 at the geometric mean of the phases
+    double lmin = 1e300, lmax = 0, mmin = 1e300, mmax = 0;
+    for (const auto& ph : c->phases) {
+      lmin = std::min(lmin, ph.lambda);
+      lmax = std::max(lmax, ph.lambda);
+      mmin = std::min(mmin, ph.mu);
+      mmax = std::max(mmax, ph.mu);
+    }
+    rpm_iso cw{c->opt.warm_c0_scale * std::sqrt(std::max(lmin, 0.0) * lmax),
+               c->opt.warm_c0_scale * std::sqrt(std::max(mmin, 0.0) * mmax)};
+    if (!(cw.mu > 0)) cw = c->c0;
+    const rpm_options saved = c->opt;
+    const rpm_iso c0_saved = c->c0;
+    c->opt.scheme = RPM_SCHEME_POLARIZATION;
+    c->opt.p_max = 0;
+    c->opt.tol = c->opt.warm_tol;
+    c->opt.max_iters = c->opt.warm_max_iters;
+    float* stage = c->fields + 5 * c->fst;        // D[0]: free until the solve proper grows Z
+    rpm_status s1 = ck(c, set_reference_medium(c, cw), "reference medium")
+                        ? solve_impl(c, E, nullptr, stage, nullptr, 0, &warm)
+                        : RPM_ERR_CUDA;
+    c->opt = saved;
+    if (!ck(c, set_reference_medium(c, c0_saved), "reference medium")) return RPM_ERR_CUDA;
+    if (s1 == RPM_ERR_CUDA || s1 == RPM_ERR_INVALID_ARG) return s1;
+    if (s1 == RPM_OK || s1 == RPM_ERR_NOT_CONVERGED) {
+      // a copy: the solve proper reuses D[0] as scratch
+      float* warm_copy = c->fields + 6 * c->fst;
+      if (!ck(c, cudaMemcpyAsync(warm_copy, stage, c->fsz * 4, cudaMemcpyDeviceToDevice, c->st),
+              "warm copy"))
+        return RPM_ERR_CUDA;
+      start = warm_copy;
+    }
+    ms_warm = warm.ms;
+    gms_warm = warm.gamma_ms;
+    pms_warm = warm.proj_ms;
+    launches_warm = warm.launches + 1;
+    pbytes_warm = warm.proj_bytes;
+    f_warm = warm.gamma_applies;
+  }
+  rpm_status s = solve_impl(c, E, start, eps_out, sig_out, out_on_host, info);
   if (s == RPM_ERR_CUDA) {
     cudaStreamSynchronize(c->st);
     if (info) info->status = s;
+  }
+  if (info && f_warm > 0) {
+    info->warm_iters = warm.iters;
+    info->warm_residual = warm.residual;
+    info->ms += ms_warm;
+    info->gamma_ms += gms_warm;
+    info->proj_ms += pms_warm;
+    info->launches += launches_warm;
+    info->proj_bytes += pbytes_warm;
+    info->gamma_applies += f_warm;
   }
   return s;
 }

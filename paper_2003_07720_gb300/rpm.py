@@ -49,7 +49,9 @@ class rpm_options(ctypes.Structure):
                 ("tol", ctypes.c_double), ("t_ratio", ctypes.c_double),
                 ("nyquist", ctypes.c_int), ("diverge_factor", ctypes.c_double),
                 ("max_device_gb", ctypes.c_double), ("profile", ctypes.c_int),
-                ("scheme", ctypes.c_int), ("alpha", ctypes.c_double), ("beta", ctypes.c_double)]
+                ("scheme", ctypes.c_int), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+                ("warm_tol", ctypes.c_double), ("warm_c0_scale", ctypes.c_double),
+                ("warm_max_iters", ctypes.c_int)]
 
 
 class rpm_solve_info(ctypes.Structure):
@@ -59,7 +61,8 @@ class rpm_solve_info(ctypes.Structure):
                 ("residual0", ctypes.c_double), ("mean_stress", ctypes.c_double * 6),
                 ("ms", ctypes.c_float), ("gamma_ms", ctypes.c_float),
                 ("proj_ms", ctypes.c_float), ("launches", ctypes.c_longlong),
-                ("proj_bytes", ctypes.c_double)]
+                ("proj_bytes", ctypes.c_double), ("warm_iters", ctypes.c_int),
+                ("warm_residual", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {"iters": self.iters, "gamma_applies": self.gamma_applies,
@@ -67,7 +70,8 @@ class rpm_solve_info(ctypes.Structure):
                 "status": self.status, "residual": self.residual,
                 "residual0": self.residual0, "mean_stress": list(self.mean_stress),
                 "ms": self.ms, "gamma_ms": self.gamma_ms, "proj_ms": self.proj_ms,
-                "launches": self.launches, "proj_bytes": self.proj_bytes}
+                "launches": self.launches, "proj_bytes": self.proj_bytes,
+                "warm_iters": self.warm_iters, "warm_residual": self.warm_residual}
 
 
 _lib = None

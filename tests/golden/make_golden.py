@@ -36,5 +36,29 @@ def softincl128():
         json.dump(out, f, indent=1)
 
 
+def softincl128_warm():
+    """The same cell, warm-started as the benchmark's headline form: the
+    Accelerated scheme (Algorithm 3, alpha = beta = 2, C0 at the geometric mean
+    of the phase moduli) to its increment 1e-4, then RPM on Eq. 3.9 to 1e-6."""
+    import numpy as np
+    cell = ms.cell_nearvoid(128, 0, c0_scale=1.0, e_incl=1e-3)
+    prob = o.Problem.from_cell(cell)
+    geo = o.Problem.from_cell(cell)
+    geo.lam0 = float(np.sqrt(cell.lam[0] * cell.lam[1]))
+    geo.mu0 = float(np.sqrt(cell.mu[0] * cell.mu[1]))
+    E = ms.unit_strain(0)
+    t0 = time.time()
+    w = o.basic_solve(geo, E, o.Options(tol=1e-4, scheme="polarization", max_iters=2000))
+    r = o.rpm_solve(prob, E, o.Options(tol=1e-6, p_max=20, n_max=10, max_iters=5000), eps0=w.eps)
+    out = {"workload": "softincl128 seed 0, E_incl 1e-3, warm start Algorithm 3 (C0 geometric "
+                       "mean) to 1e-4, then RPM (C0 = matrix) to 1e-6, p_max 20, n_max 10",
+           "warm_status": w.status, "warm_iters": w.iters, "warm_f_applies": w.f_applies,
+           "status": r.status, "iters": r.iters, "f_applies": r.f_applies + w.f_applies,
+           "basis": r.basis, "residual": r.residual,
+           "mean_stress": list(map(float, r.mean_stress)), "seconds_one_core": time.time() - t0}
+    with open(os.path.join(HERE, "softincl128_warm_oracle_solve.json"), "w") as f:
+        json.dump(out, f, indent=1)
+
+
 if __name__ == "__main__":
-    {"softincl128": softincl128}[sys.argv[1]]()
+    {"softincl128": softincl128, "softincl128_warm": softincl128_warm}[sys.argv[1]]()

@@ -230,3 +230,18 @@ def test_rpm_accelerated_solve_matches_oracle(rpm):
     assert d < CEFF_TOL * np.max(np.abs(ref.mean_stress))
     e = eps.cpu().numpy().astype(np.float64)
     assert np.linalg.norm(e - ref.eps) / np.linalg.norm(ref.eps) < FIELD_TOL
+
+
+def test_warm_started_solve_matches_cold(rpm, sphere32):
+    """Warm start by the Accelerated scheme (Algorithm 3) followed by RPM on
+    Eq. 3.9: same converged result as the cold start, within tolerance."""
+    cell, prob, ref = sphere32
+    E = ms.unit_strain(0)
+    eps = torch.empty((6,) + cell.shape, device="cuda")
+    with rpm.Context(cell, rpm.rpm_default_options(tol=1e-6, p_max=10, warm_tol=1e-4)) as ctx:
+        st, info = ctx.solve(E, eps_out=eps)
+    assert info["converged"] and info["warm_iters"] > 0 and info["warm_residual"] <= 1e-4
+    e = eps.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(e - ref.eps) / np.linalg.norm(ref.eps) < FIELD_TOL
+    d = np.max(np.abs(np.array(info["mean_stress"]) - ref.mean_stress))
+    assert d < CEFF_TOL * np.max(np.abs(ref.mean_stress))
