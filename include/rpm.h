@@ -139,8 +139,10 @@ rpm_status rpm_set_phase(rpm_ctx* ctx, const uint8_t* phase, int on_device);
 /*
  * Record the residual history of later solves: residuals[k] is the
  * fixed-point increment residual after k fixed-point steps (k = 0: initial
- * guess) and basis_sizes[k] the basis size p then, for k < capacity.  Host
- * arrays owned by the caller; either may be NULL; capacity 0 disables.
+ * guess) and basis_sizes[k] the basis size p then, for k < capacity.  While
+ * the basis is empty the solver tests (and records) the residual only every
+ * few steps; entries it skips are left untouched.  Host arrays owned by the
+ * caller; either may be NULL; capacity 0 disables.
  */
 rpm_status rpm_set_trace(rpm_ctx* ctx, double* residuals, int* basis_sizes, int capacity);
 

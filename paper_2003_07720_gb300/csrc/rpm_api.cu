@@ -27,7 +27,7 @@ constexpr int kSums = 0;              // 1 + kPCap reduced sums
 constexpr int kZa = kSums + kPCap + 8;   // reduced coordinates z (two buffers)
 constexpr int kZb = kZa + kPCap;
 constexpr int kC = kZb + kPCap;       // Newton correction c
-constexpr int kRes = kC + kPCap;      // residuals (up to kBatch)
+constexpr int kRes = kC + kPCap;      // residual
 constexpr int kBatch = 4;             // steps between host reads while the basis is empty
 constexpr int kM = kRes + 8;          // (I - H)^-1, kPCap x kPCap
 constexpr int kSmall = kM + kPCap * kPCap;
@@ -574,14 +574,6 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
   nF = 1;
 
   // residual, zeta = Z^T xi and the Newton correction for the current pair (eps, xi)
-  // residual, zeta and the Newton correction without reading them back (slot k of kRes)
-  auto eval_async = [&](int k) -> bool {
-    if (!ops.dots(xi[cur], eps_cur, c->Z, c->p, ds + kSums)) return false;
-    c->launches += 1;
-    return ck(c, launch_newton(ds + kSums, c->p, ds + kM, ds + zcur, ds + kC, ds + znext,
-                               ds + kRes + k, inv_norm, c->st),
-              "newton");
-  };
   auto eval = [&](double& r) -> bool {
     if (!ops.dots(xi[cur], eps_cur, c->Z, c->p, ds + kSums)) return false;
     c->launches += 1;
@@ -704,9 +696,8 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
       break;
     }
     // Without a basis the steps need no host decision between them: run up to
-    // kBatch of them back to back and read their residuals once (never past a
-    // basis-growth point or max_iters).  Convergence is tested on the last
-    // iterate of the batch.
+    // kBatch of them back to back and test the residual of the last one only
+    // (never past a basis-growth point or max_iters).
     int batch = 1;
     if (c->p == 0) {
       batch = kBatch;
@@ -730,23 +721,11 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
       cur = nxt;
       hist = std::min(hist + 1, 3);
       eps_cur = eps_next;
-      if (batch > 1) {
-        if (!eval_async(b)) return RPM_ERR_CUDA;
-      } else if (!eval(r)) {
-        return RPM_ERR_CUDA;
-      }
+      // with an empty basis the residual is only needed where it is tested:
+      // after the last step of the batch (a non-finite value propagates to it)
+      if (b == batch - 1 && !eval(r)) return RPM_ERR_CUDA;
     }
-    if (batch > 1) {
-      if (!ops.read_small(kRes, batch)) return RPM_ERR_CUDA;
-      for (int b = 0; b < batch; ++b) {
-        trace(it - batch + 1 + b, hs[kRes + b]);
-        if (!std::isfinite(hs[kRes + b])) r = hs[kRes + b];
-      }
-      if (std::isfinite(r)) r = hs[kRes + batch - 1];
-      if (!std::isfinite(r)) continue;            // reported as diverged at the loop top
-    } else {
-      trace(it, r);
-    }
+    trace(it, r);
     if (std::isfinite(r) && r > o.tol && r <= o.diverge_factor * r0 && nu > o.n_max) {
       if (c->p < std::min(o.p_max, c->p_cap) && hist == 3) {
         const int p_before = c->p;

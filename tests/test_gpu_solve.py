@@ -161,7 +161,9 @@ def test_nearvoid_trajectory_matches_oracle(rpm):
     assert info["basis_size"] == r.basis
     got = res[:steps + 1]
     ref = np.array(r.residuals[:steps + 1])
-    assert np.max(np.abs(got - ref) / ref) < 2e-2
+    seen = np.isfinite(got)          # with an empty basis only every few steps are tested
+    assert seen.sum() > 0.8 * steps
+    assert np.max(np.abs(got[seen] - ref[seen]) / ref[seen]) < 2e-2
     assert got[-1] > 1e-4
 
 
@@ -230,6 +232,26 @@ def test_rpm_accelerated_solve_matches_oracle(rpm):
     assert d < CEFF_TOL * np.max(np.abs(ref.mean_stress))
     e = eps.cpu().numpy().astype(np.float64)
     assert np.linalg.norm(e - ref.eps) / np.linalg.norm(ref.eps) < FIELD_TOL
+
+
+def test_softincl128_warm_solve_matches_oracle_golden(rpm):
+    """The benchmark's headline form at full size: warm start by Algorithm 3,
+    then RPM on Eq. 3.9, against the oracle's own solve of the same form
+    (tests/golden/softincl128_warm_oracle_solve.json, written by
+    tests/golden/make_golden.py from the oracle only)."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "softincl128_warm_oracle_solve.json")
+    ref = json.load(open(path))
+    cell = ms.cell_nearvoid(128, 0, e_incl=1e-3)
+    with rpm.Context(cell, rpm.rpm_default_options(tol=1e-6, p_max=20, warm_tol=1e-4)) as ctx:
+        st, info = ctx.solve(ms.unit_strain(0))
+    assert info["converged"]
+    sig = np.array(info["mean_stress"])
+    sref = np.array(ref["mean_stress"])
+    assert np.max(np.abs(sig - sref)) < CEFF_TOL * np.max(np.abs(sref)), (sig, sref)
+    assert abs(info["warm_iters"] - ref["warm_iters"]) <= 8
+    assert abs(info["gamma_applies"] - ref["f_applies"]) <= 12
 
 
 def test_warm_started_solve_matches_cold(rpm, sphere32):
