@@ -86,6 +86,7 @@ typedef struct {
   double warm_tol;
   double warm_c0_scale;  /* default 1 */
   int warm_max_iters;    /* default 2000 */
+  int warm_p_max;        /* RPM basis of the warm-start stage (default 0: plain Algorithm 3) */
 } rpm_options;
 
 /* Fixed-point map wrapped by the solver.  BASIC: Eq. 3.9 (Algorithm 1).

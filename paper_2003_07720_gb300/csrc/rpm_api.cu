@@ -104,7 +104,8 @@ bool valid_options(const rpm_options& o) {
          o.t_ratio >= 0 && o.nyquist == RPM_NYQ_ZERO_MIXED && o.diverge_factor > 0 &&
          (o.scheme == RPM_SCHEME_BASIC || o.scheme == RPM_SCHEME_POLARIZATION) &&
          std::isfinite(o.alpha) && std::isfinite(o.beta) && std::isfinite(o.warm_tol) &&
-         o.warm_c0_scale > 0 && o.warm_max_iters >= 0;
+         o.warm_c0_scale > 0 && o.warm_max_iters >= 0 && o.warm_p_max >= 0 &&
+         o.warm_p_max <= kPCap;
 }
 
 // Per-phase (lam - lam0, mu - mu0) for the polarization of pass A.
@@ -288,6 +289,7 @@ void rpm_default_options(rpm_options* o) {
   o->warm_tol = 0.0;
   o->warm_c0_scale = 1.0;
   o->warm_max_iters = 2000;
+  o->warm_p_max = 0;
 }
 
 int rpm_grid_supported(int nx, int ny, int nz) { return grid_supported(nx, ny, nz) ? 1 : 0; }
@@ -795,7 +797,7 @@ rpm_status rpm_solve(rpm_ctx* c, const double E[6], const float* eps0, float* ep
   double pbytes_warm = 0.0;
   int f_warm = 0;
   if (c->opt.warm_tol > 0 && !eps0) {
-    // stage 1: Algorithm 3 without basis, C0 at the geometric mean of the phases
+    // stage 1: Algorithm 3 (basis up to warm_p_max), C0 at the geometric mean of the phases
     double lmin = 1e300, lmax = 0, mmin = 1e300, mmax = 0;
     for (const auto& ph : c->phases) {
       lmin = std::min(lmin, ph.lambda);
@@ -809,7 +811,7 @@ rpm_status rpm_solve(rpm_ctx* c, const double E[6], const float* eps0, float* ep
     const rpm_options saved = c->opt;
     const rpm_iso c0_saved = c->c0;
     c->opt.scheme = RPM_SCHEME_POLARIZATION;
-    c->opt.p_max = 0;
+    c->opt.p_max = std::min(c->opt.warm_p_max, c->p_cap);
     c->opt.tol = c->opt.warm_tol;
     c->opt.max_iters = c->opt.warm_max_iters;
     float* stage = c->fields + 5 * c->fst;        // D[0]: free until the solve proper grows Z

@@ -51,7 +51,7 @@ class rpm_options(ctypes.Structure):
                 ("max_device_gb", ctypes.c_double), ("profile", ctypes.c_int),
                 ("scheme", ctypes.c_int), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
                 ("warm_tol", ctypes.c_double), ("warm_c0_scale", ctypes.c_double),
-                ("warm_max_iters", ctypes.c_int)]
+                ("warm_max_iters", ctypes.c_int), ("warm_p_max", ctypes.c_int)]
 
 
 class rpm_solve_info(ctypes.Structure):
