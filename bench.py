@@ -394,6 +394,42 @@ def run_gamma_only(args):
           flush=True)
 
 
+def run_study_fibre2d(args):
+    """2D fibre-in-matrix study (nz = 1, plane strain), Section 5.1 setting:
+    256^2 cell, fibre fraction 0.3 %, nu = 0.25, shear E12 = 0.5 %, contrast
+    K = 10 ... 1e5.  Iterations and device time to the increment tolerance for
+    the classical scheme, RPM, the Accelerated scheme, RPM around it, and the
+    warm-started form.  Prints one JSON line."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as entry
+    entry.build()
+    from paper_2003_07720_gb300 import rpm
+    E = np.zeros(6)
+    E[5] = 0.005
+    rows = []
+    for K in (10.0, 1e2, 1e3, 1e4, 1e5):
+        runs = {
+            "classical": ("mean", dict(p_max=0)),
+            "rpm": ("mean", dict(p_max=20)),
+            "accelerated": ("geometric", dict(p_max=0, scheme=rpm.RPM_SCHEME_POLARIZATION)),
+            "rpm_accelerated": ("geometric", dict(p_max=20, scheme=rpm.RPM_SCHEME_POLARIZATION)),
+            "warm_started": ("mean", dict(p_max=20, warm_tol=1e-4)),
+        }
+        for name, (c0, kw) in runs.items():
+            cell = ms.cell_fibre2d(256, K, c0=c0)
+            opts = rpm.rpm_default_options(tol=args.study_tol, max_iters=20000, **kw)
+            with rpm.Context(cell, opts) as ctx:
+                st, info = ctx.solve(E, raise_on_failure=False)
+            rows.append({"K": K, "method": name, "status": int(st), "iters": info["iters"],
+                         "warm_iters": info["warm_iters"], "basis": info["basis_size"],
+                         "ms": round(info["ms"], 2), "sigma12": info["mean_stress"][5],
+                         "residual": info["residual"]})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    print(json.dumps({"study": "fibre2d", "grid": [256, 256, 1], "load": "E12 = 0.005",
+                      "tol": args.study_tol, "rows": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -409,10 +445,15 @@ def main():
                          "geometric mean)")
     ap.add_argument("--max-iters", type=int, default=0,
                     help="cap the solve (profiling captures only; the result is not converged)")
+    ap.add_argument("--study", default=None, choices=[None, "fibre2d"],
+                    help="run a study instead of the benchmark")
+    ap.add_argument("--study-tol", type=float, default=1e-6)
     ap.add_argument("--kernel", default=None, choices=[None, "gamma"],
                     help="time one kernel group alone instead of the solve")
     args = ap.parse_args()
-    if args.kernel == "gamma":
+    if args.study == "fibre2d":
+        run_study_fibre2d(args)
+    elif args.kernel == "gamma":
         run_gamma_only(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -26,7 +26,7 @@ import numpy as np
 __all__ = [
     "Cell", "lame", "unit_strain", "centred_sphere", "rsa_spheres", "ellipsoids",
     "laminate", "random_two_phase", "cell_sphere32", "cell_nearvoid",
-    "cell_ellipsoids", "cell_laminate", "cell_batch_member", "BATCH_SIZES",
+    "cell_ellipsoids", "cell_laminate", "cell_batch_member", "cell_fibre2d", "BATCH_SIZES",
 ]
 
 BATCH_SIZES = (32, 48, 64, 96)
@@ -252,3 +252,25 @@ def cell_batch_member(s: int) -> Cell:
         r = max(2.0, rng.uniform(0.05, 0.10) * n)
         _stamp_sphere(mask, rng.uniform(0.0, n, size=3), r)
     return _two_phase(mask, 1.0, contrast, name=f"batch_s{s}_n{n}")
+
+
+def cell_fibre2d(n: int = 256, contrast: float = 10.0, radius: float = 1.0 / 32.0,
+                 nu: float = 0.25, c0: str = "mean") -> Cell:
+    """2D circular fibre (stiffness `contrast`, matrix E = 1, common Poisson
+    ratio nu) at the centre of a square cell, one voxel thick (nz = 1: plane
+    strain).  radius as a fraction of the cell side; 1/32 gives the 0.3 %
+    fibre fraction quoted with the Section 5 geometry.  c0: "mean" (the
+    classical rule of Section 5) or "geometric" (the Accelerated-scheme rule
+    of Section 5.5)."""
+    c = _centres(n)
+    y, x = np.meshgrid(c, c, indexing="ij")
+    d2 = _wrap(x - 0.5) ** 2 + _wrap(y - 0.5) ** 2
+    phase = (d2 < radius * radius).astype(np.uint8)[None]
+    lm, mm = lame(1.0, nu)
+    lf, mf = lame(contrast, nu)
+    if c0 == "geometric":
+        l0, m0 = lame(math.sqrt(contrast), nu)
+    else:
+        l0, m0 = lame(0.5 * (1.0 + contrast), nu)
+    return Cell(phase=phase, lam=np.array([lm, lf]), mu=np.array([mm, mf]), lam0=l0, mu0=m0,
+                name=f"fibre2d_{n}_K{contrast:g}")
