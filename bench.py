@@ -430,6 +430,56 @@ def run_study_fibre2d(args):
                       "tol": args.study_tol, "rows": rows}), flush=True)
 
 
+def run_study_batch(args):
+    """NEXT-1 measurement: C_eff of a set of batched-sweep cells (grids 32^3,
+    48^3, 64^3, 96^3; inclusion contrast within [1e-2, 1e2] so that every
+    solve converges at tol 1e-6), 6 unit loads each.  Times the cell-by-cell
+    form (one context per cell, rpm_effective_stiffness) against the batch
+    driver with 1 and with several worker streams, cold and warm-started.
+    Prints one JSON line with solves/s per form."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as entry
+    entry.build()
+    from paper_2003_07720_gb300 import rpm
+    cells = []
+    s = 0
+    while len(cells) < args.batch_cells:
+        c = ms.cell_batch_member(s)
+        k = c.mu[1] / c.mu[0]
+        if 1e-2 <= k <= 1e2:
+            cells.append(c)
+        s += 1
+    n_solves = 6 * len(cells)
+    cold = rpm.rpm_default_options(tol=TOL, p_max=P_MAX)
+    warm = rpm.rpm_default_options(tol=TOL, p_max=P_MAX, warm_tol=WARM_TOL)
+    out = {"study": "batch", "cells": [[int(x) for x in c.shape] + [float(c.mu[1] / c.mu[0])]
+                                       for c in cells], "n_solves": n_solves}
+    # warm-up (library load, kernel attributes)
+    rpm.rpm_effective_stiffness_batch(cells[:1], cold, n_workers=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    C_seq = []
+    for c in cells:
+        with rpm.Context(c, cold) as ctx:
+            C, _, _ = ctx.effective_stiffness()
+        C_seq.append(C)
+    t_seq = time.perf_counter() - t0
+    out["cell_by_cell_cold"] = {"seconds": round(t_seq, 3), "solves_per_s": round(n_solves / t_seq, 2)}
+    for name, opts, workers in (("batch_cold_1", cold, 1), ("batch_cold_w", cold, args.batch_workers),
+                                ("batch_warm_w", warm, args.batch_workers)):
+        t0 = time.perf_counter()
+        Cb, infos, stat, st = rpm.rpm_effective_stiffness_batch(cells, opts, n_workers=workers,
+                                                                raise_on_failure=False)
+        dt = time.perf_counter() - t0
+        err = max(float(np.max(np.abs(Cb[i] - C_seq[i])) / np.max(np.abs(C_seq[i])))
+                  for i in range(len(cells)))
+        out[name] = {"workers": workers, "seconds": round(dt, 3),
+                     "solves_per_s": round(n_solves / dt, 2), "status": int(st),
+                     "max_rel_diff_vs_cell_by_cell": err}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -445,14 +495,18 @@ def main():
                          "geometric mean)")
     ap.add_argument("--max-iters", type=int, default=0,
                     help="cap the solve (profiling captures only; the result is not converged)")
-    ap.add_argument("--study", default=None, choices=[None, "fibre2d"],
+    ap.add_argument("--study", default=None, choices=[None, "fibre2d", "batch"],
                     help="run a study instead of the benchmark")
     ap.add_argument("--study-tol", type=float, default=1e-6)
+    ap.add_argument("--batch-cells", type=int, default=16)
+    ap.add_argument("--batch-workers", type=int, default=8)
     ap.add_argument("--kernel", default=None, choices=[None, "gamma"],
                     help="time one kernel group alone instead of the solve")
     args = ap.parse_args()
     if args.study == "fibre2d":
         run_study_fibre2d(args)
+    elif args.study == "batch":
+        run_study_batch(args)
     elif args.kernel == "gamma":
         run_gamma_only(args)
     elif args.impl == "reference":

@@ -220,6 +220,37 @@ rpm_status rpm_solve(rpm_ctx* ctx, const double E[6], const float* eps0, float* 
  */
 rpm_status rpm_effective_stiffness(rpm_ctx* ctx, double C_eff[36], rpm_solve_info info[6]);
 
+/* Replace the phase moduli and the reference medium (same grid and phase map
+ * semantics as rpm_create; the phase map itself is kept). */
+rpm_status rpm_set_materials(rpm_ctx* ctx, int n_phases, const rpm_iso* phases, rpm_iso c0);
+
+/* One cell of a batch: grid, host phase map [nz][ny][nx], host moduli, C0. */
+typedef struct {
+  rpm_grid grid;
+  const uint8_t* phase;
+  int n_phases;
+  const rpm_iso* phases;
+  rpm_iso c0;
+} rpm_cell;
+
+/*
+ * Effective stiffness of many cells (grids may differ): the 6 x n_cells
+ * solves (cell, unit load) are taken from a queue by n_workers host threads,
+ * each with its own non-blocking CUDA stream and contexts reused per grid
+ * shape, so solves of different cells and loads run concurrently on the
+ * current device.  Each solve is the rpm_solve of `opt` (NULL: defaults).
+ *   C_eff   host double[n_cells][36] (row-major 6x6 per cell, as
+ *           rpm_effective_stiffness).
+ *   info    optional host rpm_solve_info[n_cells][6].
+ *   status  optional host int[n_cells]: RPM_OK or the first failure of the cell.
+ * Returns RPM_OK if every solve converged, else the first failure (per-cell
+ * detail in `status`); RPM_ERR_CUDA / RPM_ERR_INVALID_ARG abort the batch.
+ * Blocks until all solves finished.
+ */
+rpm_status rpm_effective_stiffness_batch(const rpm_cell* cells, int n_cells, const rpm_options* opt,
+                                         int n_workers, double* C_eff, rpm_solve_info* info,
+                                         int* status);
+
 /* Last error message of the context (never NULL). */
 const char* rpm_last_error(const rpm_ctx* ctx);
 

@@ -4,5 +4,6 @@ recursive projection method as sm_103a CUDA kernels behind a C ABI
 and the ctypes binding; it has no other implementation of the method."""
 from . import rpm  # noqa: F401
 from .rpm import (Context, RpmError, rpm_apply_gamma, rpm_create, rpm_default_options,  # noqa: F401
-                  rpm_destroy, rpm_effective_stiffness, rpm_grid_supported, rpm_set_options,
-                  rpm_set_phase, rpm_solve)
+                  rpm_destroy, rpm_effective_stiffness, rpm_effective_stiffness_batch,
+                  rpm_grid_supported, rpm_set_materials, rpm_set_options, rpm_set_phase,
+                  rpm_solve)

@@ -6,11 +6,17 @@
 // field_kernels.cu; the host only sequences launches, takes the small
 // decisions of Algorithm 2 (convergence, the one-or-two-vector rule of
 // Eq. 3.8) and inverts the p x p matrix I - H in float64.
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <thread>
+#include <tuple>
 #include <vector>
 
 #include "fft_smem.cuh"
@@ -868,6 +874,113 @@ rpm_status rpm_effective_stiffness(rpm_ctx* c, double C_eff[36], rpm_solve_info 
     if (info) info[j] = inf;
   }
   return worst;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+rpm_status rpm_set_materials(rpm_ctx* c, int n_phases, const rpm_iso* phases, rpm_iso c0) {
+  if (!c || !phases || n_phases < 1 || n_phases > 256)
+    return fail(c, RPM_ERR_INVALID_ARG, "bad phases");
+  if (!(c0.mu > 0) || !(c0.lambda + 2 * c0.mu > 0))
+    return fail(c, RPM_ERR_INVALID_ARG, "bad reference medium");
+  c->phases.assign(phases, phases + n_phases);
+  c->g.n_phases = c->gb.n_phases = n_phases;
+  std::vector<float2> cm(256, make_float2(0.f, 0.f));
+  for (int i = 0; i < n_phases; ++i)
+    cm[i] = make_float2((float)phases[i].lambda, (float)phases[i].mu);
+  if (!ck(c, cudaMemcpyAsync((void*)c->g.cmat, cm.data(), 256 * sizeof(float2),
+                             cudaMemcpyHostToDevice, c->st),
+          "materials") ||
+      !ck(c, set_reference_medium(c, c0), "reference medium"))
+    return RPM_ERR_CUDA;
+  return RPM_OK;
+}
+
+rpm_status rpm_effective_stiffness_batch(const rpm_cell* cells, int n_cells, const rpm_options* opt,
+                                         int n_workers, double* C_eff, rpm_solve_info* info,
+                                         int* status) {
+  if (!cells || n_cells < 0 || !C_eff || n_workers < 1) return RPM_ERR_INVALID_ARG;
+  for (int i = 0; i < n_cells; ++i) {
+    const rpm_cell& cl = cells[i];
+    if (!cl.phase || !cl.phases || cl.n_phases < 1 || cl.n_phases > 256) return RPM_ERR_INVALID_ARG;
+    if (!grid_supported(cl.grid.nx, cl.grid.ny, cl.grid.nz)) return RPM_ERR_UNSUPPORTED_GRID;
+  }
+  rpm_options o;
+  rpm_default_options(&o);
+  if (opt) o = *opt;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return RPM_ERR_CUDA;
+  // jobs: (cell, load); a worker keeps the cell's phase map and materials
+  // loaded while it takes consecutive loads of the same cell
+  std::atomic<int> next{0};
+  std::atomic<int> hard_error{RPM_OK};
+  const int n_jobs = 6 * n_cells;
+  std::vector<int> cell_status(n_cells, RPM_OK);
+  std::mutex status_mu;
+  auto worker = [&]() {
+    cudaSetDevice(dev);
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      hard_error = RPM_ERR_CUDA;
+      return;
+    }
+    std::map<std::tuple<int, int, int>, rpm_ctx*> ctxs;   // contexts reused per grid shape
+    int loaded_cell = -1;
+    rpm_ctx* loaded_ctx = nullptr;
+    for (;;) {
+      const int job = next.fetch_add(1);
+      if (job >= n_jobs || hard_error != RPM_OK) break;
+      const int ci = job / 6, j = job % 6;
+      const rpm_cell& cl = cells[ci];
+      const auto key = std::make_tuple(cl.grid.nx, cl.grid.ny, cl.grid.nz);
+      rpm_ctx*& ctx = ctxs[key];
+      if (!ctx) {
+        if (rpm_create(&cl.grid, cl.phase, 0, cl.n_phases, cl.phases, cl.c0, &o, st, &ctx) != RPM_OK) {
+          ctx = nullptr;
+          hard_error = RPM_ERR_CUDA;
+          break;
+        }
+        loaded_cell = ci;
+        loaded_ctx = ctx;
+      } else if (loaded_cell != ci || loaded_ctx != ctx) {
+        if (rpm_set_phase(ctx, cl.phase, 0) != RPM_OK ||
+            rpm_set_materials(ctx, cl.n_phases, cl.phases, cl.c0) != RPM_OK) {
+          hard_error = RPM_ERR_CUDA;
+          break;
+        }
+        loaded_cell = ci;
+        loaded_ctx = ctx;
+      }
+      double E[6] = {0, 0, 0, 0, 0, 0};
+      E[j] = j < 3 ? 1.0 : 0.5;
+      rpm_solve_info inf{};
+      const rpm_status s = rpm_solve(ctx, E, nullptr, nullptr, nullptr, 0, &inf);
+      if (s == RPM_ERR_CUDA || s == RPM_ERR_INVALID_ARG) {
+        hard_error = s;
+        break;
+      }
+      for (int i = 0; i < 6; ++i) C_eff[(size_t)ci * 36 + i * 6 + j] = inf.mean_stress[i];
+      if (info) info[(size_t)ci * 6 + j] = inf;
+      if (s != RPM_OK) {
+        std::lock_guard<std::mutex> lk(status_mu);
+        if (cell_status[ci] == RPM_OK) cell_status[ci] = s;
+      }
+    }
+    for (auto& kv : ctxs) rpm_destroy(kv.second);
+    cudaStreamDestroy(st);
+  };
+  std::vector<std::thread> pool;
+  const int nw = std::max(1, std::min(n_workers, n_jobs));
+  for (int w = 0; w < nw; ++w) pool.emplace_back(worker);
+  for (auto& t : pool) t.join();
+  if (status)
+    for (int i = 0; i < n_cells; ++i) status[i] = cell_status[i];
+  if (hard_error != RPM_OK) return (rpm_status)hard_error.load();
+  for (int i = 0; i < n_cells; ++i)
+    if (cell_status[i] != RPM_OK) return (rpm_status)cell_status[i];
+  return RPM_OK;
 }
 
 }  // extern "C"

@@ -74,12 +74,17 @@ class rpm_solve_info(ctypes.Structure):
                 "warm_iters": self.warm_iters, "warm_residual": self.warm_residual}
 
 
+class rpm_cell(ctypes.Structure):
+    _fields_ = [("grid", rpm_grid), ("phase", ctypes.c_void_p), ("n_phases", ctypes.c_int),
+                ("phases", ctypes.c_void_p), ("c0", rpm_iso)]
+
+
 _lib = None
 
 EXPORTS = ("rpm_default_options", "rpm_create", "rpm_set_phase", "rpm_set_options",
            "rpm_apply_gamma", "rpm_solve", "rpm_effective_stiffness", "rpm_last_error",
            "rpm_status_string", "rpm_device_bytes", "rpm_grid_supported", "rpm_destroy",
-           "rpm_set_trace")
+           "rpm_set_trace", "rpm_set_materials", "rpm_effective_stiffness_batch")
 
 
 def lib():
@@ -118,6 +123,12 @@ def lib():
     L.rpm_grid_supported.restype = ctypes.c_int
     L.rpm_set_trace.argtypes = [vp, vp, vp, ctypes.c_int]
     L.rpm_set_trace.restype = ctypes.c_int
+    L.rpm_set_materials.argtypes = [vp, ctypes.c_int, P(rpm_iso), rpm_iso]
+    L.rpm_set_materials.restype = ctypes.c_int
+    L.rpm_effective_stiffness_batch.argtypes = [P(rpm_cell), ctypes.c_int, P(rpm_options),
+                                                ctypes.c_int, P(ctypes.c_double),
+                                                P(rpm_solve_info), P(ctypes.c_int)]
+    L.rpm_effective_stiffness_batch.restype = ctypes.c_int
     L.rpm_destroy.argtypes = [vp]
     L.rpm_destroy.restype = None
     _lib = L
@@ -239,6 +250,37 @@ def rpm_set_trace(ctx, residuals, basis_sizes, capacity: int) -> None:
     """residuals: float64 numpy array, basis_sizes: int32 numpy array (host,
     kept alive by the caller)."""
     _check(ctx, lib().rpm_set_trace(ctx, _ptr(residuals), _ptr(basis_sizes), int(capacity)))
+
+
+def rpm_set_materials(ctx, phases, c0) -> None:
+    arr = (rpm_iso * len(phases))(*[rpm_iso(float(l), float(m)) for (l, m) in phases])
+    _check(ctx, lib().rpm_set_materials(ctx, len(phases), arr, rpm_iso(float(c0[0]), float(c0[1]))))
+
+
+def rpm_effective_stiffness_batch(cells, options: rpm_options | None = None, n_workers: int = 4,
+                                  raise_on_failure: bool = True):
+    """cells: objects with .phase (uint8 [nz, ny, nx]), .lam, .mu, .lam0, .mu0.
+    Returns (C_eff [n, 6, 6], infos [n][6] dicts, per-cell status, status)."""
+    n = len(cells)
+    keep = []
+    arr = (rpm_cell * max(n, 1))()
+    for i, c in enumerate(cells):
+        ph = np.ascontiguousarray(np.asarray(c.phase, dtype=np.uint8))
+        mats = (rpm_iso * len(c.lam))(*[rpm_iso(float(l), float(m)) for l, m in zip(c.lam, c.mu)])
+        keep += [ph, mats]
+        nz, ny, nx = ph.shape
+        arr[i] = rpm_cell(rpm_grid(nx, ny, nz, 1.0, 1.0, 1.0), ph.ctypes.data, len(c.lam),
+                          ctypes.cast(mats, ctypes.c_void_p).value,
+                          rpm_iso(float(c.lam0), float(c.mu0)))
+    C = (ctypes.c_double * (36 * max(n, 1)))()
+    infos = (rpm_solve_info * (6 * max(n, 1)))()
+    stat = (ctypes.c_int * max(n, 1))()
+    st = lib().rpm_effective_stiffness_batch(arr, n, ctypes.byref(options) if options else None,
+                                             int(n_workers), C, infos, stat)
+    if raise_on_failure and st != RPM_OK:
+        raise RpmError(st, "rpm_effective_stiffness_batch failed")
+    return (np.array(C[:36 * n]).reshape(n, 6, 6), [[infos[6 * i + j].as_dict() for j in range(6)]
+                                                   for i in range(n)], list(stat[:n]), st)
 
 
 def rpm_device_bytes(ctx) -> int:

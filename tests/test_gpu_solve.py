@@ -267,3 +267,26 @@ def test_warm_started_solve_matches_cold(rpm, sphere32):
     assert np.linalg.norm(e - ref.eps) / np.linalg.norm(ref.eps) < FIELD_TOL
     d = np.max(np.abs(np.array(info["mean_stress"]) - ref.mean_stress))
     assert d < CEFF_TOL * np.max(np.abs(ref.mean_stress))
+
+
+def test_effective_stiffness_batch_matches_single_contexts(rpm):
+    """NEXT-1 batch driver: cells of different grids solved concurrently on
+    worker streams give the same C_eff as one context per cell, and the
+    materials of a reused context are replaced correctly."""
+    cells = [ms.cell_sphere32(16), ms.cell_batch_member(1), ms.cell_sphere32(16)]
+    l1, m1 = ms.lame(4.0, 0.3)
+    cells[1] = ms.Cell(phase=cells[1].phase, lam=np.array([cells[1].lam[0], l1]),
+                       mu=np.array([cells[1].mu[0], m1]), lam0=0.5 * (cells[1].lam[0] + l1),
+                       mu0=0.5 * (cells[1].mu[0] + m1))
+    l2, m2 = ms.lame(25.0, 0.3)      # same grid as cell 0, other materials (context reuse)
+    cells[2] = ms.Cell(phase=cells[2].phase, lam=np.array([cells[2].lam[0], l2]),
+                       mu=np.array([cells[2].mu[0], m2]), lam0=0.5 * (cells[2].lam[0] + l2),
+                       mu0=0.5 * (cells[2].mu[0] + m2))
+    opts = rpm.rpm_default_options(tol=1e-6, p_max=10)
+    Cb, infos, stat, st = rpm.rpm_effective_stiffness_batch(cells, opts, n_workers=4)
+    assert st == rpm.RPM_OK and stat == [0, 0, 0]
+    for i, cell in enumerate(cells):
+        with rpm.Context(cell, opts) as ctx:
+            C, _, _ = ctx.effective_stiffness()
+        assert np.max(np.abs(Cb[i] - C)) <= 1e-12 * np.max(np.abs(C)), i
+    assert np.max(np.abs(Cb[0] - Cb[2])) > 1e-3      # different materials, different C_eff
