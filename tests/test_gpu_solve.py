@@ -290,3 +290,32 @@ def test_effective_stiffness_batch_matches_single_contexts(rpm):
             C, _, _ = ctx.effective_stiffness()
         assert np.max(np.abs(Cb[i] - C)) <= 1e-12 * np.max(np.abs(C)), i
     assert np.max(np.abs(Cb[0] - Cb[2])) > 1e-3      # different materials, different C_eff
+
+
+def test_degenerate_cases(rpm):
+    """E = 0 gives the zero field at once; a homogeneous cell (one phase, any
+    C0) gives eps = E after at most one step; the 2D limit nz = 1 runs."""
+    cell = ms.cell_sphere32(16)
+    eps = torch.full((6,) + cell.shape, 7.0, device="cuda")
+    with rpm.Context(cell) as ctx:
+        st, info = ctx.solve(np.zeros(6), eps_out=eps)
+    assert info["converged"] and info["iters"] == 0
+    assert float(eps.abs().max()) == 0.0
+    l, m = ms.lame(3.0, 0.3)
+    hom = ms.Cell(phase=np.zeros((8, 8, 8), np.uint8), lam=np.array([l]), mu=np.array([m]),
+                  lam0=2 * l, mu0=2 * m)
+    E = np.array([0.1, -0.2, 0.3, 0.05, 0.01, -0.04])
+    eps = torch.empty((6, 8, 8, 8), device="cuda")
+    with rpm.Context(hom) as ctx:
+        st, info = ctx.solve(E, eps_out=eps)
+    assert info["converged"] and info["iters"] <= 1
+    assert np.max(np.abs(eps.cpu().numpy() - E.reshape(6, 1, 1, 1))) < 1e-6
+    f2 = ms.cell_fibre2d(64, 10.0, radius=0.2)
+    prob = o.Problem.from_cell(f2)
+    E2 = np.zeros(6)
+    E2[5] = 0.5
+    ref = o.rpm_solve(prob, E2, o.Options(tol=1e-10, p_max=10))
+    with rpm.Context(f2, rpm.rpm_default_options(tol=1e-7, p_max=10)) as ctx:
+        st, info = ctx.solve(E2)
+    assert info["converged"]
+    assert np.max(np.abs(np.array(info["mean_stress"]) - ref.mean_stress)) < 1e-5 * np.max(np.abs(ref.mean_stress))
