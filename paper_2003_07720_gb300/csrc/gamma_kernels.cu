@@ -209,7 +209,7 @@ struct GammaArgs {
 
 template <int NZ>
 struct PencilCfg {
-  static constexpr int T = NZ >= 256 ? 4 : (NZ >= 128 ? 8 : (NZ >= 64 ? 16 : 32));
+  static constexpr int T = NZ >= 128 ? 8 : (NZ >= 64 ? 16 : 32);   // 8 pencils: 64-byte rows
   static constexpr int NZP = (NZ % 2 == 0) ? NZ + 1 : NZ;
 };
 
@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(GridDev g, float2* __restri
 // along y (inverse), rows along x (inverse).  The spectrum layout and slot
 // orders are those of the three-pass path, so pass B is shared.
 // ---------------------------------------------------------------------------
-constexpr int kRows = 16;             // rows per block in the x passes
+constexpr int kRows = 32;             // rows per block in the x passes
 constexpr int kRowsP = kRows + 1;     // odd stride
 
 template <int NX>
@@ -341,7 +341,9 @@ __global__ void __launch_bounds__(kThreads) k_rows_fwd(GridDev g, const float* _
   float2* twx = P + SX * kRowsP;
   float2* r2c = twx + NXH;
   float2* dm = r2c + SX;
-  const int y0 = blockIdx.x * kRows, z = blockIdx.y, c = blockIdx.z;
+  // component fastest: the blocks of one row block run together and share the
+  // normal components through L2
+  const int c = blockIdx.x, y0 = blockIdx.y * kRows, z = blockIdx.z;
   const int ny = g.ny;
   for (int i = threadIdx.x; i < NXH; i += blockDim.x) twx[i] = g.tw_x[i];
   for (int i = threadIdx.x; i < SX; i += blockDim.x) r2c[i] = g.r2c_w[i];
@@ -405,7 +407,7 @@ __global__ void __launch_bounds__(kThreads) k_rows_inv(GridDev g, const float2* 
   float2* P = sm;
   float2* twx = P + SX * kRowsP;
   float2* r2c = twx + NXH;
-  const int y0 = blockIdx.x * kRows, z = blockIdx.y, c = blockIdx.z;
+  const int c = blockIdx.x, y0 = blockIdx.y * kRows, z = blockIdx.z;
   const int ny = g.ny;
   for (int i = threadIdx.x; i < NXH; i += blockDim.x) twx[i] = g.tw_x[i];
   for (int i = threadIdx.x; i < SX; i += blockDim.x) r2c[i] = g.r2c_w[i];
@@ -511,7 +513,7 @@ template <int NX>
 static cudaError_t launch_rows(const GridDev& g, const float* in, float* out, float2* spec,
                                int mode, int which, cudaStream_t st) {
   constexpr int NXH = NX / 2, SX = NXH + 1;
-  const dim3 grid((g.ny + kRows - 1) / kRows, g.nz, 6);
+  const dim3 grid(6, (g.ny + kRows - 1) / kRows, g.nz);
   if (which == 0) {
     const size_t smem = (size_t)(SX * kRowsP + NXH + SX + 256) * sizeof(float2);
     cudaError_t e = set_smem(k_rows_fwd<NX>, smem);
