@@ -430,6 +430,7 @@ def run_gamma_only(args):
                       "all_ms": [round(v, 4) for v in ts],
                       "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"],
                                    "unit": "GB/s", "frac": round(ach / pk["hbm_gbs"], 4),
+                                   "traffic": recorded_traffic(f"gamma_apply_{n}"),
                                    "algorithmic_bytes_per_launch": BYTES_PER_VOXEL_GAMMA * n ** 3}}),
           flush=True)
 
