@@ -27,6 +27,7 @@ __all__ = [
     "Cell", "lame", "unit_strain", "centred_sphere", "rsa_spheres", "ellipsoids",
     "laminate", "random_two_phase", "cell_sphere32", "cell_nearvoid",
     "cell_ellipsoids", "cell_laminate", "cell_batch_member", "cell_fibre2d", "BATCH_SIZES",
+    "cell_fno_member", "fno_params", "strain_direction",
 ]
 
 BATCH_SIZES = (32, 48, 64, 96)
@@ -274,3 +275,44 @@ def cell_fibre2d(n: int = 256, contrast: float = 10.0, radius: float = 1.0 / 32.
         l0, m0 = lame(0.5 * (1.0 + contrast), nu)
     return Cell(phase=phase, lam=np.array([lm, lf]), mu=np.array([mm, mf]), lam0=l0, mu0=m0,
                 name=f"fibre2d_{n}_K{contrast:g}")
+
+
+def cell_fno_member(s: int, n: int = 64) -> Cell:
+    """Training / test cell s of the learned warm start: the batched-sweep
+    recipe (spheres of radius U[0.05, 0.10] n voxels, min 2, to a volume
+    fraction U(0.1, 0.35), contrast 10^U(-6, 3), C0 at the mean modulus) on a
+    fixed n^3 grid.  Seeds 1000-2999 train, 5000-5019 test."""
+    rng = np.random.Generator(np.random.PCG64(20_000 + s))
+    vf = rng.uniform(0.1, 0.35)
+    contrast = 10.0 ** rng.uniform(-6.0, 3.0)
+    mask = np.zeros((n, n, n), np.uint8)
+    while mask.mean() < vf:
+        r = max(2.0, rng.uniform(0.05, 0.10) * n)
+        _stamp_sphere(mask, rng.uniform(0.0, n, size=3), r)
+    return _two_phase(mask, 1.0, contrast, name=f"fno_s{s}_n{n}")
+
+
+def strain_direction(s: int) -> np.ndarray:
+    """Macroscopic strain direction s: a Gaussian 6-vector scaled to unit
+    Frobenius norm of the tensor (shear components counted twice)."""
+    rng = np.random.Generator(np.random.PCG64(30_000 + s))
+    e = rng.standard_normal(6)
+    w = np.array([1.0, 1.0, 1.0, 2.0, 2.0, 2.0])
+    return e / math.sqrt(float(np.sum(w * e * e)))
+
+
+def fno_params(modes: int, layers: int, seed: int = 0, width: int = 16, cin: int = 8,
+               cout: int = 6) -> dict:
+    """Random parameters of the spectral neural operator: dense maps
+    N(0, 1 / fan_in), biases zero, spectral weights with real and imaginary
+    parts uniform in [0, 1 / width^2); R{l} is complex [in][out][4 modes^3]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    M = 4 * modes ** 3
+    p = {"P": rng.standard_normal((width, cin)) / math.sqrt(cin), "p": np.zeros(width),
+         "Q": rng.standard_normal((cout, width)) / math.sqrt(width), "q": np.zeros(cout)}
+    for l in range(layers):
+        p[f"A{l}"] = rng.standard_normal((width, width)) / math.sqrt(width)
+        p[f"a{l}"] = np.zeros(width)
+        p[f"R{l}"] = (rng.random((width, width, M)) + 1j * rng.random((width, width, M))) / (
+            width * width)
+    return p

@@ -262,6 +262,18 @@ def apply_F(prob: Problem, eps: np.ndarray, E) -> np.ndarray:
     return xi + E.reshape(6, 1, 1, 1)
 
 
+def project_compatible(prob: Problem, eps: np.ndarray, E) -> np.ndarray:
+    """E + Gamma0 * (C0 : eps): the field of mean E whose fluctuation is the
+    compatible part of eps's fluctuation (Section 2: Gamma0 C0 acts as the
+    identity on compatible fluctuations and Gamma0 annihilates equilibrated
+    stress fluctuations).  Used to clean a warm-start guess."""
+    E = np.asarray(E, float)
+    tr = eps[0] + eps[1] + eps[2]
+    tau0 = 2.0 * prob.mu0 * eps
+    tau0[:3] += prob.lam0 * tr[None]
+    return E.reshape(6, 1, 1, 1) - apply_gamma_raw(prob, tau0)
+
+
 def apply_F_classical(prob: Problem, eps: np.ndarray, E) -> np.ndarray:
     """Eq. (3.9) as printed: F^-1[F[eps] - Gamma0_hat : F[C : eps]], with the
     zero frequency set to E (Algorithm 1)."""

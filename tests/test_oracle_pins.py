@@ -481,3 +481,25 @@ def test_polarization_solution_is_fixed_point_and_solvers_converge(tiny, alpha, 
     for r in (o.basic_solve(p, E, o.Options(**kw)), o.rpm_solve(p, E, o.Options(p_max=20, **kw))):
         assert r.converged
         assert np.max(np.abs(r.eps - ref)) < 1e-8
+
+
+def test_compatible_projection_fixes_compatible_fields_and_is_idempotent():
+    """project_compatible(E + e) = E + e for compatible zero-mean e; applied
+    to any field it gives mean E, a compatible fluctuation, and is idempotent."""
+    shape = (8, 8, 6)
+    p = _prob(shape)
+    E = np.array([0.01, -0.02, 0.005, 0.003, -0.004, 0.002])
+    e = _compatible_field(shape)
+    f = E.reshape(6, 1, 1, 1) + e
+    assert np.max(np.abs(o.project_compatible(p, f, E) - f)) < 1e-12 * np.max(np.abs(f))
+    g = _rng(21).standard_normal((6,) + shape)
+    pg = o.project_compatible(p, g, E)
+    assert np.allclose(pg.reshape(6, -1).mean(axis=1), E, atol=1e-13)
+    assert np.max(np.abs(o.project_compatible(p, pg, E) - pg)) < 1e-12 * np.max(np.abs(pg))
+    xi, _, _ = o.frequencies(p)
+    eta = _incompatibility(o.fft_fields(pg - E.reshape(6, 1, 1, 1)), xi)
+    assert np.max(np.abs(eta)) < 1e-9 * np.max(np.abs(o.fft_fields(pg))) * np.max(np.abs(xi)) ** 2
+    # the projection does not depend on the phases, only on C0
+    p2 = o.Problem(phase=np.zeros(shape, np.uint8), lam=np.array([1.0]), mu=np.array([1.0]),
+                   lam0=p.lam0, mu0=p.mu0)
+    assert np.allclose(o.project_compatible(p2, g, E), pg, atol=1e-14)
