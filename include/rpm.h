@@ -87,6 +87,8 @@ typedef struct {
   double warm_c0_scale;  /* default 1 */
   int warm_max_iters;    /* default 2000 */
   int warm_p_max;        /* RPM basis of the warm-start stage (default 0: plain Algorithm 3) */
+  int warm_from_eps0;    /* 0 (default): a caller eps0 replaces the warm-start stage;
+                            1: the stage runs from eps0 (e.g. a learned guess) */
 } rpm_options;
 
 /* Fixed-point map wrapped by the solver.  BASIC: Eq. 3.9 (Algorithm 1).
@@ -153,7 +155,10 @@ rpm_status rpm_set_options(rpm_ctx* ctx, const rpm_options* opt);
 enum {
   RPM_GAMMA_FULL_MAP = 0, /* out = F(in) = E - Gamma0 * ((C - C0) : in), Eq. 3.9, 2.4-2.5 */
   RPM_GAMMA_LINEAR = 1,   /* out = F_u in = -Gamma0 * ((C - C0) : in)  (E ignored) */
-  RPM_GAMMA_RAW_TAU = 2   /* out = -Gamma0 * in, `in` being a polarization tau (E ignored) */
+  RPM_GAMMA_RAW_TAU = 2,  /* out = -Gamma0 * in, `in` being a polarization tau (E ignored) */
+  RPM_GAMMA_PROJECT = 3   /* out = E + Gamma0 * (C0 : in): the compatible strain field with
+                             mean E nearest to `in` in the C0 energy (Sec. 2: Gamma0 C0 is
+                             the projector onto compatible fluctuations); rpm_apply_gamma only */
 };
 
 /*

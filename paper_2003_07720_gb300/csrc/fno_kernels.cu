@@ -1,0 +1,1037 @@
+// Learned warm start: a 3D spectral neural operator (truncated-Fourier layers),
+// forward, backward and Adam, as declared in include/rpm_fno.h.
+//
+// One Fourier layer on B samples of W = 16 channels over an N^3 grid runs as
+// three kernels:
+//   k_xy_fwd    block per (z, b): for each channel, the x transform of the
+//               plane restricted to kx < m, then the y transform restricted to
+//               the 2m kept ky; writes the [ncol = 2m * m][W] mode columns of
+//               the plane.
+//   k_spec_fwd  block per kept (ky, kx) column, looping over the batch: z
+//               transform to the 2m kept kz, complex channel mixing with the
+//               column's R (held in shared memory), inverse z transform.
+//   k_inv_xy    block per (y chunk, z, b): inverse y then inverse x transform
+//               of the 16 channels, fused with the pointwise branch
+//               A v + a and the activation (forward) or with the accumulation
+//               of the input gradient (backward).
+// The transforms are truncated DFTs (sums over the N points for each kept
+// frequency, twiddles from one table of N roots): with m = 12 kept modes of
+// N = 64 points the truncated sums cost about what a full FFT would and
+// produce only the coefficients that are used.
+//
+// Parameter gradients of the pointwise maps (P, A_l, Q and biases) are
+// outer-product sums over all voxels: each block accumulates them over tiles
+// of 256 voxels staged in shared memory and writes one partial row; a second
+// kernel adds the rows in a fixed order (float64), so gradients are
+// deterministic.  Gradients of R_l are accumulated by the block that owns the
+// (ky, kx) column, over the batch, in registers.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rpm.h"
+#include "rpm_fno.h"
+#include "rpm_internal.h"
+
+namespace {
+
+constexpr int W = RPM_FNO_WIDTH;   // channels of the hidden layers
+constexpr int CV = 2;              // voxel features
+constexpr int CE = 6;              // broadcast strain components
+constexpr int CIN = CV + CE;
+constexpr int COUT = 6;
+constexpr int kMaxModes = RPM_FNO_MAX_MODES;
+constexpr int kThreads = 256;
+constexpr int kHeader = 256;       // floats before layer 0 in the parameter vector
+constexpr int kLayerHead = W * W + W;
+constexpr int kPwBlocksMax = 4 * 152;
+constexpr float kGeluC = 0.7978845608028654f;   // sqrt(2 / pi)
+
+// offsets of the head parameters
+constexpr int kOffP = 0;
+constexpr int kOffQ = W * CIN + W;               // 144
+constexpr int kNeA = W * W + W;                  // gradient entries of (A, a)
+constexpr int kNeQ = COUT * W + COUT;            // (Q, q)
+constexpr int kNeP = W * CIN + W;                // (P, p)
+constexpr int kNeHead = kNeQ + 1;                // + squared-error sum
+
+size_t r_floats(int m) { return (size_t)2 * (2 * m * m) * (2 * m) * W * W; }
+size_t layer_floats(int m) { return kLayerHead + r_floats(m); }
+size_t layer_off(int m, int l) { return kHeader + (size_t)l * layer_floats(m); }
+
+__device__ __forceinline__ int kfreq(int i, int m, int N) { return i < m ? i : N - 2 * m + i; }
+
+__device__ __forceinline__ float gelu(float x) {
+  return 0.5f * x * (1.f + tanhf(kGeluC * (x + 0.044715f * x * x * x)));
+}
+__device__ __forceinline__ float gelu_grad(float x) {
+  const float t = tanhf(kGeluC * (x + 0.044715f * x * x * x));
+  return 0.5f * (1.f + t) + 0.5f * x * (1.f - t * t) * kGeluC * (1.f + 3.f * 0.044715f * x * x);
+}
+
+// ---------------------------------------------------------------------------
+// Transforms
+// ---------------------------------------------------------------------------
+
+// shared-memory carve-up of k_xy_fwd (floats)
+__host__ __device__ inline size_t xy_plane_floats(int N) { return ((size_t)N * (N + 1) + 3) / 4 * 4; }
+size_t xy_smem(int N, int m) {
+  return (xy_plane_floats(N) + 2 * ((size_t)N * m + (size_t)2 * m * m * W + N)) * 4;
+}
+
+// src [B][W][N][N][N] -> dst [B][N(z)][ncol][W] (complex); column = ky_i * m + kx.
+// tw[j] = exp(-2 pi i j / N).
+__global__ void __launch_bounds__(kThreads) k_xy_fwd(const float* __restrict__ src,
+                                                     float2* __restrict__ dst,
+                                                     const float2* __restrict__ twg, int N, int m) {
+  extern __shared__ float4 smem4[];
+  const int P = N + 1;
+  const int ncol = 2 * m * m;
+  float* plane = (float*)smem4;
+  float2* X = (float2*)(plane + xy_plane_floats(N));   // [y][kx]
+  float2* acc = X + N * m;                             // [ncol][W]
+  float2* tw = acc + ncol * W;                         // [N]
+  const int tid = threadIdx.x, z = blockIdx.x, b = blockIdx.y;
+  const long long NN = (long long)N * N;
+  for (int i = tid; i < N; i += kThreads) tw[i] = twg[i];
+  for (int c = 0; c < W; ++c) {
+    const float* s = src + (((long long)b * W + c) * N + z) * NN;
+    __syncthreads();
+    for (int i = tid; i < N * N; i += kThreads) plane[(i / N) * P + i % N] = s[i];
+    __syncthreads();
+    for (int o = tid; o < N * m; o += kThreads) {
+      const int y = o / m, kx = o - (o / m) * m;
+      const float* row = plane + y * P;
+      float re = 0.f, im = 0.f;
+      int j = 0;
+      for (int x = 0; x < N; ++x) {
+        const float2 t = tw[j];
+        re = fmaf(row[x], t.x, re);
+        im = fmaf(row[x], t.y, im);
+        j += kx;
+        if (j >= N) j -= N;
+      }
+      X[o] = make_float2(re, im);
+    }
+    __syncthreads();
+    for (int o = tid; o < ncol; o += kThreads) {
+      const int kyi = o / m, kx = o - (o / m) * m;
+      const int ky = kfreq(kyi, m, N);
+      float re = 0.f, im = 0.f;
+      int j = 0;
+      for (int y = 0; y < N; ++y) {
+        const float2 v = X[y * m + kx], t = tw[j];
+        re += v.x * t.x - v.y * t.y;
+        im += v.x * t.y + v.y * t.x;
+        j += ky;
+        if (j >= N) j -= N;
+      }
+      acc[o * W + c] = make_float2(re, im);
+    }
+  }
+  __syncthreads();
+  float2* d = dst + ((long long)b * N + z) * ncol * W;
+  for (int i = tid; i < ncol * W; i += kThreads) d[i] = acc[i];
+}
+
+size_t spec_smem(int N, int m) {
+  const size_t m2 = 2 * m;
+  return (m2 * W * W + (size_t)N * W + 3 * m2 * W + N) * sizeof(float2);
+}
+
+// z transform of the column's [N][W] values to the 2m kept kz: out[kz_i][c].
+__device__ __forceinline__ void z_dft(const float2* a, const float2* tw, float2* out, int N, int m,
+                                      float scale) {
+  for (int o = threadIdx.x; o < 2 * m * W; o += kThreads) {
+    const int kzi = o / W, c = o % W;
+    const int kz = kfreq(kzi, m, N);
+    float re = 0.f, im = 0.f;
+    int j = 0;
+    for (int z = 0; z < N; ++z) {
+      const float2 v = a[z * W + c], t = tw[j];
+      re += v.x * t.x - v.y * t.y;
+      im += v.x * t.y + v.y * t.x;
+      j += kz;
+      if (j >= N) j -= N;
+    }
+    out[o] = make_float2(scale * re, scale * im);
+  }
+}
+
+// inverse z transform (no weights) of U[kz_i][c] to dst[z][c] (column stride given).
+__device__ __forceinline__ void z_idft(const float2* U, const float2* tw, float2* dst,
+                                       long long zstride, int N, int m) {
+  for (int o = threadIdx.x; o < N * W; o += kThreads) {
+    const int z = o / W, c = o % W;
+    float re = 0.f, im = 0.f;
+    for (int kzi = 0; kzi < 2 * m; ++kzi) {
+      const int kz = kfreq(kzi, m, N);
+      const float2 u = U[kzi * W + c], t = tw[(kz * z) % N];
+      re += u.x * t.x + u.y * t.y;   // u * conj(t)
+      im += u.y * t.x - u.x * t.y;
+    }
+    dst[(long long)z * zstride + c] = make_float2(re, im);
+  }
+}
+
+// A2 [B][N][ncol][W] -> V (saved, [ncol][B][2m][W]), U = V R, Bz [B][N][ncol][W].
+__global__ void __launch_bounds__(kThreads) k_spec_fwd(const float2* __restrict__ A2,
+                                                       const float2* __restrict__ R,
+                                                       float2* __restrict__ Vs,
+                                                       float2* __restrict__ Bz,
+                                                       const float2* __restrict__ twg, int N, int m,
+                                                       int B) {
+  extern __shared__ float4 smem4[];
+  const int m2 = 2 * m, ncol = 2 * m * m, col = blockIdx.x, tid = threadIdx.x;
+  float2* Rs = (float2*)smem4;      // [kz_i][i][o]
+  float2* a = Rs + m2 * W * W;      // [z][c]
+  float2* V = a + N * W;            // [kz_i][c]
+  float2* U = V + m2 * W;
+  float2* tw = U + m2 * W;
+  const float4* r4 = (const float4*)(R + (long long)col * m2 * W * W);
+  for (int i = tid; i < m2 * W * W / 2; i += kThreads) ((float4*)Rs)[i] = r4[i];
+  for (int i = tid; i < N; i += kThreads) tw[i] = twg[i];
+  for (int b = 0; b < B; ++b) {
+    __syncthreads();
+    for (int i = tid; i < N * W; i += kThreads)
+      a[i] = A2[((long long)b * N + i / W) * ncol * W + col * W + i % W];
+    __syncthreads();
+    z_dft(a, tw, V, N, m, 1.f);
+    __syncthreads();
+    float2* vs = Vs + ((long long)col * B + b) * m2 * W;
+    for (int o = tid; o < m2 * W; o += kThreads) {
+      vs[o] = V[o];
+      const int kzi = o / W, oc = o % W;
+      float re = 0.f, im = 0.f;
+#pragma unroll
+      for (int i = 0; i < W; ++i) {
+        const float2 v = V[kzi * W + i], r = Rs[(kzi * W + i) * W + oc];
+        re += v.x * r.x - v.y * r.y;
+        im += v.x * r.y + v.y * r.x;
+      }
+      U[o] = make_float2(re, im);
+    }
+    __syncthreads();
+    z_idft(U, tw, Bz + (long long)b * N * ncol * W + col * W, (long long)ncol * W, N, m);
+  }
+}
+
+// Backward of k_spec_fwd.  A2 holds the xy transform of dz; dU = w(kx) / N^3 *
+// (z transform); gR[col] = sum_b dU conj(V); dV = sum_o dU conj(R); Bz = inverse z of dV.
+__global__ void __launch_bounds__(kThreads) k_spec_bwd(const float2* __restrict__ A2,
+                                                       const float2* __restrict__ R,
+                                                       const float2* __restrict__ Vs,
+                                                       float2* __restrict__ gR,
+                                                       float2* __restrict__ Bz,
+                                                       const float2* __restrict__ twg, int N, int m,
+                                                       int B, float inv_n3) {
+  extern __shared__ float4 smem4[];
+  const int m2 = 2 * m, ncol = 2 * m * m, col = blockIdx.x, tid = threadIdx.x;
+  float2* Rs = (float2*)smem4;
+  float2* a = Rs + m2 * W * W;
+  float2* dU = a + N * W;
+  float2* V = dU + m2 * W;
+  float2* dV = V + m2 * W;
+  float2* tw = dV + m2 * W;
+  const int kx = col % m;
+  const float wgt = (kx == 0 ? 1.f : 2.f) * inv_n3;
+  const float4* r4 = (const float4*)(R + (long long)col * m2 * W * W);
+  for (int i = tid; i < m2 * W * W / 2; i += kThreads) ((float4*)Rs)[i] = r4[i];
+  for (int i = tid; i < N; i += kThreads) tw[i] = twg[i];
+  const int gi = tid / W, go = tid % W;   // this thread's (i, o) entry of gR
+  float2 g[2 * kMaxModes];
+#pragma unroll
+  for (int k = 0; k < 2 * kMaxModes; ++k) g[k] = make_float2(0.f, 0.f);
+  for (int b = 0; b < B; ++b) {
+    __syncthreads();
+    for (int i = tid; i < N * W; i += kThreads)
+      a[i] = A2[((long long)b * N + i / W) * ncol * W + col * W + i % W];
+    const float2* vs = Vs + ((long long)col * B + b) * m2 * W;
+    for (int o = tid; o < m2 * W; o += kThreads) V[o] = vs[o];
+    __syncthreads();
+    z_dft(a, tw, dU, N, m, wgt);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 2 * kMaxModes; ++k)
+      if (k < m2) {
+        const float2 u = dU[k * W + go], v = V[k * W + gi];
+        g[k].x += u.x * v.x + u.y * v.y;   // u * conj(v)
+        g[k].y += u.y * v.x - u.x * v.y;
+      }
+    for (int o = tid; o < m2 * W; o += kThreads) {
+      const int kzi = o / W, i = o % W;
+      float re = 0.f, im = 0.f;
+#pragma unroll
+      for (int s = 0; s < W; ++s) {
+        const int oc = (s + i) & (W - 1);   // rotated: conflict-free rows of Rs
+        const float2 u = dU[kzi * W + oc], r = Rs[(kzi * W + i) * W + oc];
+        re += u.x * r.x + u.y * r.y;        // u * conj(r)
+        im += u.y * r.x - u.x * r.y;
+      }
+      dV[o] = make_float2(re, im);
+    }
+    __syncthreads();
+    z_idft(dV, tw, Bz + (long long)b * N * ncol * W + col * W, (long long)ncol * W, N, m);
+  }
+  float2* gr = gR + (long long)col * m2 * W * W;
+#pragma unroll
+  for (int k = 0; k < 2 * kMaxModes; ++k)
+    if (k < m2) gr[k * W * W + tid] = g[k];
+}
+
+size_t inv_smem(int m, int YC) {
+  return ((size_t)2 * m * m * W + (size_t)YC * m * W + RPM_FNO_MAX_N) * sizeof(float2) +
+         kLayerHead * sizeof(float);
+}
+
+// Inverse y and x transforms of the mode columns of plane (z, b), rows
+// [y0, y0 + YC), fused with the pointwise part of the layer.
+//   BWD = false: z = A v + a + u (u weighted c(kx) / N^3); writes zsave (unless
+//                last) and vout = gelu(z) (z on the last layer).
+//   BWD = true : vout += u (unweighted).
+template <bool BWD>
+__global__ void __launch_bounds__(kThreads) k_inv_xy(const float2* __restrict__ Bz,
+                                                     const float2* __restrict__ twg,
+                                                     const float* __restrict__ layer,
+                                                     const float* __restrict__ vin,
+                                                     float* __restrict__ zsave,
+                                                     float* __restrict__ vout, int N, int m,
+                                                     int YC, int last, float inv_n3) {
+  extern __shared__ float4 smem4[];
+  const int ncol = 2 * m * m, tid = threadIdx.x;
+  float2* S = (float2*)smem4;          // [ncol][W]
+  float2* Y = S + ncol * W;            // [yy][kx][c]
+  float2* tw = Y + YC * m * W;         // [N]
+  float* Al = (float*)(tw + RPM_FNO_MAX_N);   // A [o][c], a [o]
+  const int y0 = blockIdx.x * YC, z = blockIdx.y, b = blockIdx.z;
+  const long long N3 = (long long)N * N * N;
+  const float2* src = Bz + ((long long)b * N + z) * ncol * W;
+  for (int i = tid; i < ncol * W / 2; i += kThreads) ((float4*)S)[i] = ((const float4*)src)[i];
+  for (int i = tid; i < N; i += kThreads) tw[i] = twg[i];
+  if (!BWD)
+    for (int i = tid; i < kLayerHead; i += kThreads) Al[i] = layer[i];
+  __syncthreads();
+  for (int o = tid; o < YC * m * W; o += kThreads) {
+    const int yy = o / (m * W), r = o - yy * (m * W), kx = r / W, c = r % W;
+    const int y = y0 + yy;
+    float re = 0.f, im = 0.f;
+    for (int kyi = 0; kyi < 2 * m; ++kyi) {
+      const int ky = kfreq(kyi, m, N);
+      const float2 s = S[(kyi * m + kx) * W + c], t = tw[(ky * y) % N];
+      re += s.x * t.x + s.y * t.y;   // s * conj(t)
+      im += s.y * t.x - s.x * t.y;
+    }
+    Y[o] = make_float2(re, im);
+  }
+  __syncthreads();
+  for (int o = tid; o < YC * N; o += kThreads) {
+    const int yy = o / N, x = o - yy * N;
+    float u[W];
+#pragma unroll
+    for (int c = 0; c < W; ++c) u[c] = 0.f;
+    int j = 0;
+    for (int kx = 0; kx < m; ++kx) {
+      const float2 t = tw[j];
+      const float w = BWD ? 1.f : (kx == 0 ? inv_n3 : 2.f * inv_n3);
+      const float cr = w * t.x, ci = w * t.y;   // Re(Y e^{+i phi}) = Yr cos + Yi sin
+      const float2* yr = Y + (yy * m + kx) * W;
+#pragma unroll
+      for (int c = 0; c < W; ++c) u[c] += yr[c].x * cr + yr[c].y * ci;
+      j += x;
+      if (j >= N) j -= N;
+    }
+    const long long vox = ((long long)z * N + y0 + yy) * N + x;
+    if (BWD) {
+#pragma unroll
+      for (int c = 0; c < W; ++c) vout[((long long)b * W + c) * N3 + vox] += u[c];
+    } else {
+      float v[W];
+#pragma unroll
+      for (int c = 0; c < W; ++c) v[c] = vin[((long long)b * W + c) * N3 + vox];
+#pragma unroll
+      for (int oc = 0; oc < W; ++oc) {
+        float s = Al[W * W + oc] + u[oc];
+#pragma unroll
+        for (int c = 0; c < W; ++c) s = fmaf(Al[oc * W + c], v[c], s);
+        const long long at = ((long long)b * W + oc) * N3 + vox;
+        if (last) {
+          vout[at] = s;
+        } else {
+          zsave[at] = s;
+          vout[at] = gelu(s);
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pointwise maps with parameter-gradient partial sums
+// ---------------------------------------------------------------------------
+
+// Per-block accumulation of sum_j L[a][j] R[b][j] (NA x NB) and sum_j L[a][j]
+// over tiles of kThreads voxels staged in shared memory (row stride
+// kThreads + 1: conflict-free column reads).
+template <int NA, int NB>
+struct TileAcc {
+  static constexpr int NE = NA * NB + NA;
+  static constexpr int PER = (NE + kThreads - 1) / kThreads;
+  static constexpr int LD = kThreads + 1;
+  float acc[PER];
+  __device__ void init() {
+#pragma unroll
+    for (int k = 0; k < PER; ++k) acc[k] = 0.f;
+  }
+  // all threads call this once per tile, after writing column threadIdx.x of sL / sR
+  __device__ void step(const float* sL, const float* sR) {
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int e = threadIdx.x + k * kThreads;
+      if (e < NA * NB) {
+        const float* l = sL + (e / NB) * LD;
+        const float* r = sR + (e % NB) * LD;
+        float s = 0.f;
+        for (int j = 0; j < kThreads; ++j) s = fmaf(l[j], r[j], s);
+        acc[k] += s;
+      } else if (e < NE) {
+        const float* l = sL + (e - NA * NB) * LD;
+        float s = 0.f;
+        for (int j = 0; j < kThreads; ++j) s += l[j];
+        acc[k] += s;
+      }
+    }
+  }
+  __device__ void store(float* part) const {
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int e = threadIdx.x + k * kThreads;
+      if (e < NE) part[e] = acc[k];
+    }
+  }
+};
+
+// v0 = P [f; E_b] + p.   total = B N^3 voxels.
+__global__ void __launch_bounds__(kThreads) k_lift(const float* __restrict__ feat,
+                                                   const float* __restrict__ Ed,
+                                                   const float* __restrict__ prm,
+                                                   float* __restrict__ v0, long long N3, int B) {
+  __shared__ float Ps[kNeP];
+  for (int i = threadIdx.x; i < kNeP; i += kThreads) Ps[i] = prm[kOffP + i];
+  __syncthreads();
+  const long long total = N3 * B;
+  for (long long gidx = blockIdx.x * (long long)kThreads + threadIdx.x; gidx < total;
+       gidx += (long long)gridDim.x * kThreads) {
+    const int b = (int)(gidx / N3);
+    const long long vox = gidx - b * N3;
+    float x[CIN];
+    x[0] = feat[((long long)b * CV + 0) * N3 + vox];
+    x[1] = feat[((long long)b * CV + 1) * N3 + vox];
+#pragma unroll
+    for (int e = 0; e < CE; ++e) x[CV + e] = Ed[b * CE + e];
+#pragma unroll 4
+    for (int o = 0; o < W; ++o) {
+      float s = Ps[W * CIN + o];
+#pragma unroll
+      for (int c = 0; c < CIN; ++c) s = fmaf(Ps[o * CIN + c], x[c], s);
+      v0[((long long)b * W + o) * N3 + vox] = s;
+    }
+  }
+}
+
+// Tile loop shared by the gradient kernels: every block runs the same number
+// of tiles; a thread without a voxel contributes zeros.
+#define RPM_FNO_TILE_LOOP(total)                                                        \
+  for (long long base = (long long)blockIdx.x * kThreads; base < (total);              \
+       base += (long long)gridDim.x * kThreads)
+
+// Gradient of the lift: gP = sum dv0 [f; E_b]^T, gp = sum dv0.
+__global__ void __launch_bounds__(kThreads) k_lift_bwd(const float* __restrict__ dv0,
+                                                       const float* __restrict__ feat,
+                                                       const float* __restrict__ Ed,
+                                                       float* __restrict__ part, long long N3,
+                                                       int B) {
+  using Acc = TileAcc<W, CIN>;
+  __shared__ float sL[W * Acc::LD];
+  __shared__ float sR[CIN * Acc::LD];
+  Acc acc;
+  acc.init();
+  const long long total = N3 * B;
+  const int t = threadIdx.x;
+  RPM_FNO_TILE_LOOP(total) {
+    const long long gidx = base + t;
+    if (gidx < total) {
+      const int b = (int)(gidx / N3);
+      const long long vox = gidx - b * N3;
+#pragma unroll
+      for (int o = 0; o < W; ++o) sL[o * Acc::LD + t] = dv0[((long long)b * W + o) * N3 + vox];
+      sR[0 * Acc::LD + t] = feat[((long long)b * CV + 0) * N3 + vox];
+      sR[1 * Acc::LD + t] = feat[((long long)b * CV + 1) * N3 + vox];
+#pragma unroll
+      for (int e = 0; e < CE; ++e) sR[(CV + e) * Acc::LD + t] = Ed[b * CE + e];
+    } else {
+#pragma unroll
+      for (int o = 0; o < W; ++o) sL[o * Acc::LD + t] = 0.f;
+#pragma unroll
+      for (int c = 0; c < CIN; ++c) sR[c * Acc::LD + t] = 0.f;
+    }
+    __syncthreads();
+    acc.step(sL, sR);
+    __syncthreads();
+  }
+  acc.store(part + (long long)blockIdx.x * Acc::NE);
+}
+
+// Backward through layer l's pointwise part: dz = dv * gelu'(z) (dv on the last
+// layer), dvprev = A^T dz, partials of gA = sum dz v^T and ga = sum dz.
+__global__ void __launch_bounds__(kThreads) k_bwd_pw(const float* __restrict__ dv,
+                                                     const float* __restrict__ zs,
+                                                     const float* __restrict__ v,
+                                                     const float* __restrict__ layer,
+                                                     float* __restrict__ dz,
+                                                     float* __restrict__ dvprev,
+                                                     float* __restrict__ part, long long N3,
+                                                     int B, int last) {
+  using Acc = TileAcc<W, W>;
+  __shared__ float sL[W * Acc::LD];
+  __shared__ float sR[W * Acc::LD];
+  __shared__ float As[W * W];
+  for (int i = threadIdx.x; i < W * W; i += kThreads) As[i] = layer[i];
+  __syncthreads();
+  Acc acc;
+  acc.init();
+  const long long total = N3 * B;
+  const int t = threadIdx.x;
+  RPM_FNO_TILE_LOOP(total) {
+    const long long gidx = base + t;
+    if (gidx < total) {
+      const int b = (int)(gidx / N3);
+      const long long vox = gidx - b * N3;
+      float d[W];
+#pragma unroll
+      for (int o = 0; o < W; ++o) {
+        const long long at = ((long long)b * W + o) * N3 + vox;
+        float g = dv[at];
+        if (!last) g *= gelu_grad(zs[at]);
+        d[o] = g;
+        dz[at] = g;
+        sL[o * Acc::LD + t] = g;
+        sR[o * Acc::LD + t] = v[at];
+      }
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        float s = 0.f;
+#pragma unroll
+        for (int o = 0; o < W; ++o) s = fmaf(As[o * W + c], d[o], s);
+        dvprev[((long long)b * W + c) * N3 + vox] = s;
+      }
+    } else {
+#pragma unroll
+      for (int o = 0; o < W; ++o) {
+        sL[o * Acc::LD + t] = 0.f;
+        sR[o * Acc::LD + t] = 0.f;
+      }
+    }
+    __syncthreads();
+    acc.step(sL, sR);
+    __syncthreads();
+  }
+  acc.store(part + (long long)blockIdx.x * Acc::NE);
+}
+
+// Projection out = oscale (Q v + q); with a target: d = 2 (out - t) / nel,
+// dvL = Q^T d, partials of gQ = sum d v^T, gq = sum d and of sum (out - t)^2.
+__global__ void __launch_bounds__(kThreads) k_head(const float* __restrict__ v,
+                                                   const float* __restrict__ prm,
+                                                   const float* __restrict__ target,
+                                                   float* __restrict__ out,
+                                                   float* __restrict__ dv,
+                                                   float* __restrict__ part, long long N3, int B,
+                                                   float oscale, float inv_nel) {
+  using Acc = TileAcc<COUT, W>;
+  __shared__ float sL[COUT * Acc::LD];
+  __shared__ float sR[W * Acc::LD];
+  __shared__ float Qs[kNeQ];
+  __shared__ float red[kThreads / 32];
+  for (int i = threadIdx.x; i < kNeQ; i += kThreads) Qs[i] = prm[kOffQ + i];
+  __syncthreads();
+  Acc acc;
+  acc.init();
+  float sq = 0.f;
+  const long long total = N3 * B;
+  const int t = threadIdx.x;
+  RPM_FNO_TILE_LOOP(total) {
+    const long long gidx = base + t;
+    const bool have = gidx < total;
+    if (have) {
+      const int b = (int)(gidx / N3);
+      const long long vox = gidx - b * N3;
+      float x[W];
+#pragma unroll
+      for (int c = 0; c < W; ++c) x[c] = v[((long long)b * W + c) * N3 + vox];
+      float d[COUT];
+#pragma unroll
+      for (int o = 0; o < COUT; ++o) {
+        float s = Qs[COUT * W + o];
+#pragma unroll
+        for (int c = 0; c < W; ++c) s = fmaf(Qs[o * W + c], x[c], s);
+        s *= oscale;
+        const long long at = ((long long)b * COUT + o) * N3 + vox;
+        if (out) out[at] = s;
+        if (target) {
+          const float diff = s - target[at];
+          sq = fmaf(diff, diff, sq);
+          d[o] = 2.f * diff * inv_nel;
+        }
+      }
+      if (target) {
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+          float s = 0.f;
+#pragma unroll
+          for (int o = 0; o < COUT; ++o) s = fmaf(Qs[o * W + c], d[o], s);
+          dv[((long long)b * W + c) * N3 + vox] = s;
+          sR[c * Acc::LD + t] = x[c];
+        }
+#pragma unroll
+        for (int o = 0; o < COUT; ++o) sL[o * Acc::LD + t] = d[o];
+      }
+    }
+    if (target) {
+      if (!have) {
+#pragma unroll
+        for (int o = 0; o < COUT; ++o) sL[o * Acc::LD + t] = 0.f;
+#pragma unroll
+        for (int c = 0; c < W; ++c) sR[c * Acc::LD + t] = 0.f;
+      }
+      __syncthreads();
+      acc.step(sL, sR);
+      __syncthreads();
+    }
+  }
+  if (!target) return;
+  acc.store(part + (long long)blockIdx.x * kNeHead);
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if ((t & 31) == 0) red[t >> 5] = sq;
+  __syncthreads();
+  if (t == 0) {
+    float s = 0.f;
+    for (int w = 0; w < kThreads / 32; ++w) s += red[w];
+    part[(long long)blockIdx.x * kNeHead + kNeQ] = s;
+  }
+}
+
+// dst[e] = sum over blocks of part[blk][e] (float64, fixed order) for e < n_grad;
+// the entries after n_grad go to extra (float64).
+__global__ void k_reduce(const float* __restrict__ part, int nblk, int stride, int n_grad,
+                         int n_extra, float* __restrict__ dst, double* __restrict__ extra) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_grad + n_extra) return;
+  double s = 0.0;
+  for (int k = 0; k < nblk; ++k) s += (double)part[(long long)k * stride + e];
+  if (e < n_grad)
+    dst[e] = (float)s;
+  else
+    extra[e - n_grad] = s;
+}
+
+// Adam with bias correction and decoupled weight decay.
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m1,
+                       float* __restrict__ m2, long long n, float lr, float b1, float b2,
+                       float eps, float wd, float bc1, float bc2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float a = b1 * m1[i] + (1.f - b1) * gi;
+    const float b = b2 * m2[i] + (1.f - b2) * gi * gi;
+    m1[i] = a;
+    m2[i] = b;
+    p[i] -= lr * ((a / bc1) / (sqrtf(b / bc2) + eps) + wd * p[i]);
+  }
+}
+
+// Voxel features from a phase map: log10(Young / Young(phase 0)), Poisson ratio.
+__global__ void k_features(const uint8_t* __restrict__ phase, const float2* __restrict__ tab,
+                           long long n, float* __restrict__ feat) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float2 t = tab[phase[i]];
+    feat[i] = t.x;
+    feat[n + i] = t.y;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+struct rpm_fno {
+  int N = 0, m = 0, L = 0, Bmax = 0, ncol = 0, YC = 8;
+  long long N3 = 0;
+  size_t nparam = 0;
+  cudaStream_t st = nullptr;
+  float* params = nullptr;
+  float* grads = nullptr;
+  float* adam1 = nullptr;
+  float* adam2 = nullptr;
+  float* acts = nullptr;      // v_0..v_L, then z_0..z_{L-2}
+  float* dvbuf = nullptr;     // two gradient buffers and dz
+  float2* A2 = nullptr;
+  float2* Bz = nullptr;
+  float2* Vs = nullptr;       // per layer [ncol][Bmax][2m][W]
+  float2* tw = nullptr;
+  float* part = nullptr;
+  double* extra = nullptr;
+  float* Ed = nullptr;        // [Bmax][6]
+  float* hE = nullptr;        // pinned staging of E
+  double* hloss = nullptr;    // pinned
+  float* feat1 = nullptr;     // warm start: features and output of one sample
+  float* out1 = nullptr;
+  float2* ftab = nullptr;     // feature table per phase id (256)
+  cudaEvent_t ev = nullptr;
+  long long step = 0;
+  size_t bytes = 0;
+  std::string err;
+
+  size_t act_floats() const { return (size_t)Bmax * W * N3; }
+  float* v(int l) const { return acts + (size_t)l * act_floats(); }
+  float* z(int l) const { return acts + (size_t)(L + 1 + l) * act_floats(); }
+  float* dvb(int k) const { return dvbuf + (size_t)k * act_floats(); }
+  float2* Vsl(int l) const { return Vs + (size_t)l * ncol * Bmax * 2 * m * W; }
+  float* layer(int l) const { return params + layer_off(m, l); }
+  float* glayer(int l) const { return grads + layer_off(m, l); }
+};
+
+namespace {
+
+rpm_status ffail(rpm_fno* f, rpm_status s, const std::string& msg) {
+  if (f) f->err = msg;
+  return s;
+}
+
+bool fck(rpm_fno* f, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return true;
+  f->err = std::string(what) + ": " + cudaGetErrorString(e);
+  return false;
+}
+
+int pw_blocks(long long total) {
+  const long long t = (total + kThreads - 1) / kThreads;
+  return (int)std::max(1LL, std::min<long long>(kPwBlocksMax, t));
+}
+
+cudaError_t set_smem(const void* k, size_t bytes) {
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+bool stage_E(rpm_fno* f, int B, const float* E_dir) {
+  std::memcpy(f->hE, E_dir, sizeof(float) * CE * B);
+  return fck(f, cudaMemcpyAsync(f->Ed, f->hE, sizeof(float) * CE * B, cudaMemcpyHostToDevice,
+                                f->st),
+             "E");
+}
+
+// Forward pass; keeps v_l and z_l.  out (optional), target (optional: then the
+// head also writes dv_L into dvb(0) and its partials).
+bool run_forward(rpm_fno* f, int B, const float* feat, const float* target, float* out,
+                 float oscale) {
+  const int N = f->N, m = f->m, L = f->L;
+  const long long total = f->N3 * B;
+  const int nb = pw_blocks(total);
+  const float inv_n3 = 1.f / (float)f->N3;
+  k_lift<<<nb, kThreads, 0, f->st>>>(feat, f->Ed, f->params, f->v(0), f->N3, B);
+  if (!fck(f, cudaGetLastError(), "lift")) return false;
+  for (int l = 0; l < L; ++l) {
+    k_xy_fwd<<<dim3(N, B), kThreads, xy_smem(N, m), f->st>>>(f->v(l), f->A2, f->tw, N, m);
+    k_spec_fwd<<<f->ncol, kThreads, spec_smem(N, m), f->st>>>(
+        f->A2, (const float2*)(f->layer(l) + kLayerHead), f->Vsl(l), f->Bz, f->tw, N, m, B);
+    const int last = (l == L - 1);
+    k_inv_xy<false><<<dim3(N / f->YC, N, B), kThreads, inv_smem(m, f->YC), f->st>>>(
+        f->Bz, f->tw, f->layer(l), f->v(l), last ? nullptr : f->z(l), f->v(l + 1), N, m, f->YC,
+        last, inv_n3);
+    if (!fck(f, cudaGetLastError(), "layer")) return false;
+  }
+  const float inv_nel = 1.f / (float)(total * COUT);
+  k_head<<<nb, kThreads, 0, f->st>>>(f->v(L), f->params, target, out, f->dvb(0), f->part,
+                                     f->N3, B, oscale, inv_nel);
+  if (!fck(f, cudaGetLastError(), "head")) return false;
+  if (target) {
+    k_reduce<<<1, 128, 0, f->st>>>(f->part, nb, kNeHead, kNeQ, 1, f->grads + kOffQ, f->extra);
+    if (!fck(f, cudaGetLastError(), "reduce head")) return false;
+  }
+  return true;
+}
+
+bool run_backward(rpm_fno* f, int B, const float* feat) {
+  const int N = f->N, m = f->m, L = f->L;
+  const long long total = f->N3 * B;
+  const int nb = pw_blocks(total);
+  const float inv_n3 = 1.f / (float)f->N3;
+  int cur = 0;   // dvb(cur) holds dL/dv_{l+1}
+  for (int l = L - 1; l >= 0; --l) {
+    const int last = (l == L - 1);
+    float* dz = f->dvb(2);
+    float* prev = f->dvb(1 - cur);
+    k_bwd_pw<<<nb, kThreads, 0, f->st>>>(f->dvb(cur), last ? nullptr : f->z(l), f->v(l),
+                                         f->layer(l), dz, prev, f->part, f->N3, B, last);
+    k_reduce<<<(kNeA + 127) / 128, 128, 0, f->st>>>(f->part, nb, kNeA, kNeA, 0, f->glayer(l),
+                                                    nullptr);
+    k_xy_fwd<<<dim3(N, B), kThreads, xy_smem(N, m), f->st>>>(dz, f->A2, f->tw, N, m);
+    k_spec_bwd<<<f->ncol, kThreads, spec_smem(N, m), f->st>>>(
+        f->A2, (const float2*)(f->layer(l) + kLayerHead), f->Vsl(l),
+        (float2*)(f->glayer(l) + kLayerHead), f->Bz, f->tw, N, m, B, inv_n3);
+    k_inv_xy<true><<<dim3(N / f->YC, N, B), kThreads, inv_smem(m, f->YC), f->st>>>(
+        f->Bz, f->tw, nullptr, nullptr, nullptr, prev, N, m, f->YC, 0, inv_n3);
+    if (!fck(f, cudaGetLastError(), "layer backward")) return false;
+    cur = 1 - cur;
+  }
+  k_lift_bwd<<<nb, kThreads, 0, f->st>>>(f->dvb(cur), feat, f->Ed, f->part, f->N3, B);
+  k_reduce<<<(kNeP + 127) / 128, 128, 0, f->st>>>(f->part, nb, kNeP, kNeP, 0, f->grads + kOffP,
+                                                  nullptr);
+  return fck(f, cudaGetLastError(), "lift backward");
+}
+
+bool valid_batch(rpm_fno* f, int B) { return f && B >= 1 && B <= f->Bmax; }
+
+}  // namespace
+
+extern "C" {
+
+size_t rpm_fno_param_count(int modes, int layers) {
+  if (modes < 1 || modes > kMaxModes || layers < 1 || layers > RPM_FNO_MAX_LAYERS) return 0;
+  return layer_off(modes, layers);
+}
+
+rpm_status rpm_fno_create(const rpm_fno_config* cfg, void* cuda_stream, rpm_fno** out) {
+  if (!cfg || !out) return RPM_ERR_INVALID_ARG;
+  *out = nullptr;
+  const int N = cfg->n, m = cfg->modes, L = cfg->layers, B = cfg->max_batch;
+  if (m < 1 || m > kMaxModes || L < 1 || L > RPM_FNO_MAX_LAYERS || B < 1 || N < 24 ||
+      N > RPM_FNO_MAX_N || N % 8 != 0 || N < 2 * m)
+    return RPM_ERR_INVALID_ARG;
+  rpm_fno* f = new rpm_fno();
+  f->N = N;
+  f->m = m;
+  f->L = L;
+  f->Bmax = B;
+  f->ncol = 2 * m * m;
+  f->N3 = (long long)N * N * N;
+  f->nparam = rpm_fno_param_count(m, L);
+  f->st = (cudaStream_t)cuda_stream;
+  f->YC = (N <= 64 && N % 16 == 0) ? 16 : 8;   // rows per k_inv_xy block (divides N)
+  auto alloc = [&](void** p, size_t b) {
+    cudaError_t e = cudaMalloc(p, std::max<size_t>(b, 256));
+    if (e == cudaSuccess) f->bytes += b;
+    return e == cudaSuccess;
+  };
+  const size_t P = f->nparam * sizeof(float);
+  const size_t act = f->act_floats() * sizeof(float);
+  const size_t colb = (size_t)B * N * f->ncol * W * sizeof(float2);
+  const size_t vsb = (size_t)L * f->ncol * B * 2 * m * W * sizeof(float2);
+  const size_t partb = (size_t)kPwBlocksMax * kNeA * sizeof(float);   // largest row
+  const bool ok =
+      alloc((void**)&f->params, P) && alloc((void**)&f->grads, P) &&
+      alloc((void**)&f->adam1, P) && alloc((void**)&f->adam2, P) &&
+      alloc((void**)&f->acts, act * (2 * L)) && alloc((void**)&f->dvbuf, act * 3) &&
+      alloc((void**)&f->A2, colb) && alloc((void**)&f->Bz, colb) && alloc((void**)&f->Vs, vsb) &&
+      alloc((void**)&f->tw, N * sizeof(float2)) && alloc((void**)&f->part, partb) &&
+      alloc((void**)&f->extra, 64) && alloc((void**)&f->Ed, B * CE * sizeof(float)) &&
+      alloc((void**)&f->feat1, f->N3 * CV * sizeof(float)) &&
+      alloc((void**)&f->out1, f->N3 * COUT * sizeof(float)) &&
+      alloc((void**)&f->ftab, 256 * sizeof(float2));
+  if (!ok || cudaMallocHost((void**)&f->hE, B * CE * sizeof(float)) != cudaSuccess ||
+      cudaMallocHost((void**)&f->hloss, 64) != cudaSuccess ||
+      cudaEventCreateWithFlags(&f->ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    rpm_fno_destroy(f);
+    return RPM_ERR_OOM;
+  }
+  std::vector<float2> tw(N);
+  for (int j = 0; j < N; ++j) {
+    const double a = -2.0 * M_PI * (double)j / (double)N;
+    tw[j] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  const size_t smax = std::max(xy_smem(N, m), std::max(spec_smem(N, m), inv_smem(m, f->YC)));
+  if (smax > 227 * 1024 ||
+      cudaMemcpyAsync(f->tw, tw.data(), N * sizeof(float2), cudaMemcpyHostToDevice, f->st) !=
+          cudaSuccess ||
+      cudaMemsetAsync(f->params, 0, P, f->st) != cudaSuccess ||
+      cudaMemsetAsync(f->grads, 0, P, f->st) != cudaSuccess ||
+      cudaMemsetAsync(f->adam1, 0, P, f->st) != cudaSuccess ||
+      cudaMemsetAsync(f->adam2, 0, P, f->st) != cudaSuccess ||
+      // the attribute is per kernel, not per network: allow the largest configuration
+      set_smem((const void*)k_xy_fwd, xy_smem(RPM_FNO_MAX_N, kMaxModes)) != cudaSuccess ||
+      set_smem((const void*)k_spec_fwd, spec_smem(RPM_FNO_MAX_N, kMaxModes)) != cudaSuccess ||
+      set_smem((const void*)k_spec_bwd, spec_smem(RPM_FNO_MAX_N, kMaxModes)) != cudaSuccess ||
+      set_smem((const void*)k_inv_xy<false>, inv_smem(kMaxModes, 16)) != cudaSuccess ||
+      set_smem((const void*)k_inv_xy<true>, inv_smem(kMaxModes, 16)) != cudaSuccess ||
+      cudaStreamSynchronize(f->st) != cudaSuccess) {
+    cudaGetLastError();
+    rpm_fno_destroy(f);
+    return RPM_ERR_CUDA;
+  }
+  *out = f;
+  return RPM_OK;
+}
+
+rpm_status rpm_fno_set_params(rpm_fno* f, const float* params) {
+  if (!f || !params) return ffail(f, RPM_ERR_INVALID_ARG, "null argument");
+  const size_t P = f->nparam * sizeof(float);
+  if (!fck(f, cudaMemcpyAsync(f->params, params, P, cudaMemcpyHostToDevice, f->st), "params") ||
+      !fck(f, cudaMemsetAsync(f->adam1, 0, P, f->st), "adam") ||
+      !fck(f, cudaMemsetAsync(f->adam2, 0, P, f->st), "adam") ||
+      !fck(f, cudaStreamSynchronize(f->st), "sync"))
+    return RPM_ERR_CUDA;
+  f->step = 0;
+  return RPM_OK;
+}
+
+static rpm_status copy_out(rpm_fno* f, const float* src, float* dst) {
+  if (!f || !dst) return ffail(f, RPM_ERR_INVALID_ARG, "null argument");
+  if (!fck(f, cudaMemcpyAsync(dst, src, f->nparam * sizeof(float), cudaMemcpyDeviceToHost, f->st),
+           "copy") ||
+      !fck(f, cudaStreamSynchronize(f->st), "sync"))
+    return RPM_ERR_CUDA;
+  return RPM_OK;
+}
+
+rpm_status rpm_fno_get_params(rpm_fno* f, float* params) {
+  return copy_out(f, f ? f->params : nullptr, params);
+}
+
+rpm_status rpm_fno_get_grads(rpm_fno* f, float* grads) {
+  return copy_out(f, f ? f->grads : nullptr, grads);
+}
+
+rpm_status rpm_fno_forward(rpm_fno* f, int batch, const float* feat, const float* E_dir,
+                           float* out) {
+  if (!valid_batch(f, batch) || !feat || !E_dir || !out)
+    return ffail(f, RPM_ERR_INVALID_ARG, "bad forward arguments");
+  if (!stage_E(f, batch, E_dir) || !run_forward(f, batch, feat, nullptr, out, 1.f))
+    return RPM_ERR_CUDA;
+  return RPM_OK;
+}
+
+rpm_status rpm_fno_loss_grad(rpm_fno* f, int batch, const float* feat, const float* E_dir,
+                             const float* target, double* loss) {
+  if (!valid_batch(f, batch) || !feat || !E_dir || !target)
+    return ffail(f, RPM_ERR_INVALID_ARG, "bad loss_grad arguments");
+  if (!stage_E(f, batch, E_dir) || !run_forward(f, batch, feat, target, nullptr, 1.f) ||
+      !run_backward(f, batch, feat))
+    return RPM_ERR_CUDA;
+  if (loss) {
+    if (!fck(f, cudaMemcpyAsync(f->hloss, f->extra, 8, cudaMemcpyDeviceToHost, f->st), "loss") ||
+        !fck(f, cudaStreamSynchronize(f->st), "sync"))
+      return RPM_ERR_CUDA;
+    *loss = f->hloss[0] / ((double)f->N3 * batch * COUT);
+  }
+  return RPM_OK;
+}
+
+rpm_status rpm_fno_adam_step(rpm_fno* f, const rpm_fno_adam* o) {
+  if (!f || !o || !(o->lr >= 0) || !(o->beta1 >= 0 && o->beta1 < 1) ||
+      !(o->beta2 >= 0 && o->beta2 < 1) || !(o->eps > 0) || !(o->weight_decay >= 0))
+    return ffail(f, RPM_ERR_INVALID_ARG, "bad Adam options");
+  ++f->step;
+  const float bc1 = (float)(1.0 - std::pow((double)o->beta1, (double)f->step));
+  const float bc2 = (float)(1.0 - std::pow((double)o->beta2, (double)f->step));
+  k_adam<<<4 * 152, 256, 0, f->st>>>(f->params, f->grads, f->adam1, f->adam2,
+                                     (long long)f->nparam, o->lr, o->beta1, o->beta2, o->eps,
+                                     o->weight_decay, bc1, bc2);
+  return fck(f, cudaGetLastError(), "adam") ? RPM_OK : RPM_ERR_CUDA;
+}
+
+rpm_status rpm_fno_train_step(rpm_fno* f, int batch, const float* feat, const float* E_dir,
+                              const float* target, const rpm_fno_adam* opt, double* loss) {
+  if (!opt) return ffail(f, RPM_ERR_INVALID_ARG, "null Adam options");
+  rpm_status s = rpm_fno_loss_grad(f, batch, feat, E_dir, target, loss);
+  if (s != RPM_OK) return s;
+  return rpm_fno_adam_step(f, opt);
+}
+
+static rpm_status features_on(const uint8_t* phase, long long n, int n_phases,
+                              const rpm_iso* phases, float* feat, float2* tab_dev,
+                              cudaStream_t st) {
+  std::vector<float2> tab(256, make_float2(0.f, 0.f));
+  const double l0 = phases[0].lambda, m0 = phases[0].mu;
+  const double y0 = m0 * (3 * l0 + 2 * m0) / (l0 + m0);
+  for (int i = 0; i < n_phases; ++i) {
+    const double l = phases[i].lambda, m = phases[i].mu;
+    const double y = m * (3 * l + 2 * m) / (l + m);
+    tab[i] = make_float2((float)std::log10(y / y0), (float)(l / (2 * (l + m))));
+  }
+  if (cudaMemcpyAsync(tab_dev, tab.data(), 256 * sizeof(float2), cudaMemcpyHostToDevice, st) !=
+      cudaSuccess)
+    return RPM_ERR_CUDA;
+  k_features<<<4 * 152, 256, 0, st>>>(phase, tab_dev, n, feat);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+    return RPM_ERR_CUDA;
+  return RPM_OK;
+}
+
+static bool valid_moduli(int n_phases, const rpm_iso* phases) {
+  if (n_phases < 1 || n_phases > 256 || !phases) return false;
+  for (int i = 0; i < n_phases; ++i)
+    if (!(phases[i].mu > 0) || !(phases[i].lambda + phases[i].mu > 0)) return false;
+  return true;
+}
+
+rpm_status rpm_fno_features(const uint8_t* phase, long long n, int n_phases,
+                            const rpm_iso* phases, float* feat, void* cuda_stream) {
+  if (!phase || !feat || n < 1 || !valid_moduli(n_phases, phases)) return RPM_ERR_INVALID_ARG;
+  float2* tab = nullptr;
+  if (cudaMalloc((void**)&tab, 256 * sizeof(float2)) != cudaSuccess) return RPM_ERR_OOM;
+  const rpm_status s =
+      features_on(phase, n, n_phases, phases, feat, tab, (cudaStream_t)cuda_stream);
+  cudaFree(tab);
+  return s;
+}
+
+rpm_status rpm_fno_warm_start(rpm_fno* f, rpm_ctx* ctx, const double E[6], float* eps0) {
+  if (!f || !ctx || !E || !eps0) return ffail(f, RPM_ERR_INVALID_ARG, "null argument");
+  rpm::CellView cv{};
+  if (!rpm::ctx_cell_view(ctx, &cv)) return ffail(f, RPM_ERR_INVALID_ARG, "bad context");
+  if (cv.nx != f->N || cv.ny != f->N || cv.nz != f->N)
+    return ffail(f, RPM_ERR_INVALID_ARG, "context grid differs from the network grid");
+  if (!valid_moduli(cv.n_phases, cv.phases)) return ffail(f, RPM_ERR_INVALID_ARG, "bad moduli");
+  double nrm = 0;
+  for (int k = 0; k < 6; ++k) nrm += (k < 3 ? 1.0 : 2.0) * E[k] * E[k];
+  nrm = std::sqrt(nrm);
+  if (!(nrm > 0) || !std::isfinite(nrm)) return ffail(f, RPM_ERR_INVALID_ARG, "E must be nonzero");
+  // the phase map is written on the context stream: order the network after it
+  if (!fck(f, cudaEventRecord(f->ev, cv.st), "event") ||
+      !fck(f, cudaStreamWaitEvent(f->st, f->ev, 0), "event"))
+    return RPM_ERR_CUDA;
+  if (features_on(cv.phase, f->N3, cv.n_phases, cv.phases, f->feat1, f->ftab, f->st) != RPM_OK)
+    return ffail(f, RPM_ERR_CUDA, "features");
+  float e[6];
+  for (int k = 0; k < 6; ++k) e[k] = (float)(E[k] / nrm);
+  if (!stage_E(f, 1, e) || !run_forward(f, 1, f->feat1, nullptr, f->out1, (float)nrm) ||
+      !fck(f, cudaStreamSynchronize(f->st), "sync"))
+    return RPM_ERR_CUDA;
+  const rpm_status s = rpm_apply_gamma(ctx, f->out1, E, eps0, RPM_GAMMA_PROJECT);
+  if (s != RPM_OK) return ffail(f, s, std::string("projection: ") + rpm_last_error(ctx));
+  if (!fck(f, cudaStreamSynchronize(cv.st), "sync")) return RPM_ERR_CUDA;
+  return RPM_OK;
+}
+
+size_t rpm_fno_device_bytes(const rpm_fno* f) { return f ? f->bytes : 0; }
+
+const char* rpm_fno_last_error(const rpm_fno* f) { return f ? f->err.c_str() : "null network"; }
+
+void rpm_fno_destroy(rpm_fno* f) {
+  if (!f) return;
+  void* dev[] = {f->params, f->grads, f->adam1, f->adam2, f->acts,  f->dvbuf, f->A2, f->Bz,
+                 f->Vs,     f->tw,    f->part,  f->extra, f->Ed,    f->feat1, f->out1, f->ftab};
+  for (void* p : dev)
+    if (p) cudaFree(p);
+  if (f->hE) cudaFreeHost(f->hE);
+  if (f->hloss) cudaFreeHost(f->hloss);
+  if (f->ev) cudaEventDestroy(f->ev);
+  delete f;
+}
+
+}  // extern "C"

@@ -53,6 +53,8 @@ struct rpm_ctx {
   GridDev gb{};                      // g with the Algorithm 3 pre-step table (s_b)
   float2* dmat_b = nullptr;          // per phase (alpha lam - beta lam0, alpha mu - beta mu0)
   float4* post = nullptr;            // per phase (lam_a, mu_a, lam_s, mu_s) of Algorithm 3
+  GridDev gp{};                      // g with the table (-lam0, -mu0): compatible projection
+  float2* dmat_p = nullptr;
   long long n = 0;
   size_t fsz = 0;                    // floats per field (6 n)
   size_t fst = 0;                    // stride between internal fields (6 n + pad)
@@ -111,7 +113,7 @@ bool valid_options(const rpm_options& o) {
          (o.scheme == RPM_SCHEME_BASIC || o.scheme == RPM_SCHEME_POLARIZATION) &&
          std::isfinite(o.alpha) && std::isfinite(o.beta) && std::isfinite(o.warm_tol) &&
          o.warm_c0_scale > 0 && o.warm_max_iters >= 0 && o.warm_p_max >= 0 &&
-         o.warm_p_max <= kPCap;
+         o.warm_p_max <= kPCap && (o.warm_from_eps0 == 0 || o.warm_from_eps0 == 1);
 }
 
 // Per-phase (lam - lam0, mu - mu0) for the polarization of pass A.
@@ -129,8 +131,8 @@ cudaError_t upload_scheme_tables(rpm_ctx* c);
 // Switch the reference medium C0 of the context (tables and Green operator).
 cudaError_t set_reference_medium(rpm_ctx* c, rpm_iso c0) {
   c->c0 = c0;
-  c->g.lam0 = c->gb.lam0 = (float)c0.lambda;
-  c->g.mu0 = c->gb.mu0 = (float)c0.mu;
+  c->g.lam0 = c->gb.lam0 = c->gp.lam0 = (float)c0.lambda;
+  c->g.mu0 = c->gb.mu0 = c->gp.mu0 = (float)c0.mu;
   cudaError_t e = upload_dmat(c);
   if (e != cudaSuccess) return e;
   return upload_scheme_tables(c);
@@ -142,6 +144,8 @@ cudaError_t upload_scheme_tables(rpm_ctx* c) {
   std::vector<float2> db(256, make_float2(0.f, 0.f));
   std::vector<float4> pt(256, make_float4(0.f, 0.f, 1.f, 1.f));
   const double a = c->opt.alpha, b = c->opt.beta, l0 = c->c0.lambda, m0 = c->c0.mu;
+  // projection table: (C - C0) replaced by -C0 for every phase id
+  std::vector<float2> dp(256, make_float2((float)-l0, (float)-m0));
   for (size_t i = 0; i < c->phases.size(); ++i) {
     const double l = c->phases[i].lambda, m = c->phases[i].mu;
     db[i] = make_float2((float)(a * l - b * l0), (float)(a * m - b * m0));
@@ -152,6 +156,8 @@ cudaError_t upload_scheme_tables(rpm_ctx* c) {
                                   cudaMemcpyHostToDevice, c->st);
   if (e != cudaSuccess) return e;
   e = cudaMemcpyAsync(c->post, pt.data(), 256 * sizeof(float4), cudaMemcpyHostToDevice, c->st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(c->dmat_p, dp.data(), 256 * sizeof(float2), cudaMemcpyHostToDevice, c->st);
   if (e != cudaSuccess) return e;
   return cudaStreamSynchronize(c->st);
 }
@@ -296,6 +302,7 @@ void rpm_default_options(rpm_options* o) {
   o->warm_c0_scale = 1.0;
   o->warm_max_iters = 2000;
   o->warm_p_max = 0;
+  o->warm_from_eps0 = 0;
 }
 
 int rpm_grid_supported(int nx, int ny, int nz) { return grid_supported(nx, ny, nz) ? 1 : 0; }
@@ -317,6 +324,22 @@ const char* rpm_status_string(rpm_status s) {
 const char* rpm_last_error(const rpm_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 size_t rpm_device_bytes(const rpm_ctx* c) { return c ? c->bytes : 0; }
+
+}  // extern "C"
+
+bool rpm::ctx_cell_view(const rpm_ctx* c, CellView* v) {
+  if (!c || !v || c->phases.empty()) return false;
+  v->nx = c->grid.nx;
+  v->ny = c->grid.ny;
+  v->nz = c->grid.nz;
+  v->phase = c->phase;
+  v->phases = c->phases.data();
+  v->n_phases = (int)c->phases.size();
+  v->st = c->st;
+  return true;
+}
+
+extern "C" {
 
 void rpm_destroy(rpm_ctx* c) {
   if (!c) return;
@@ -355,7 +378,7 @@ rpm_status rpm_set_options(rpm_ctx* c, const rpm_options* o) {
     return fail(c, RPM_ERR_INVALID_ARG, "invalid options (p_max above the creation value?)");
   c->opt = *o;
   c->g.nyquist = o->nyquist;
-  c->gb.nyquist = o->nyquist;
+  c->gb.nyquist = c->gp.nyquist = o->nyquist;
   if (!ck(c, upload_scheme_tables(c), "scheme tables")) return RPM_ERR_CUDA;
   return RPM_OK;
 }
@@ -436,6 +459,7 @@ rpm_status rpm_create(const rpm_grid* grid, const uint8_t* phase, int phase_on_d
   const size_t o_cm = off; off = align_up(off + 256 * 8, 256);
   const size_t o_db = off; off = align_up(off + 256 * 8, 256);
   const size_t o_pt = off; off = align_up(off + 256 * 16, 256);
+  const size_t o_dp = off; off = align_up(off + 256 * 8, 256);
   const size_t tab_bytes = off;
   c->nblk = std::max(dots_blocks_for(c->n), stress_blocks_for(c->n));
   const size_t fbytes = c->fst * sizeof(float);
@@ -504,8 +528,11 @@ rpm_status rpm_create(const rpm_grid* grid, const uint8_t* phase, int phase_on_d
   g.phase = c->phase;
   c->dmat_b = (float2*)(t + o_db);
   c->post = (float4*)(t + o_pt);
+  c->dmat_p = (float2*)(t + o_dp);
   c->gb = g;
   c->gb.dmat = c->dmat_b;
+  c->gp = g;
+  c->gp.dmat = c->dmat_p;
   if (!ck(c, upload_scheme_tables(c), "scheme tables")) {
     rpm_destroy(c);
     return RPM_ERR_CUDA;
@@ -530,10 +557,18 @@ rpm_status rpm_set_trace(rpm_ctx* c, double* residuals, int* basis_sizes, int ca
 
 rpm_status rpm_apply_gamma(rpm_ctx* c, const float* in, const double E[6], float* out, int flags) {
   if (!c || !in || !out) return fail(c, RPM_ERR_INVALID_ARG, "null argument");
-  if (flags < RPM_GAMMA_FULL_MAP || flags > RPM_GAMMA_RAW_TAU)
+  if (flags < RPM_GAMMA_FULL_MAP || flags > RPM_GAMMA_PROJECT)
     return fail(c, RPM_ERR_INVALID_ARG, "bad flags");
-  if (flags == RPM_GAMMA_FULL_MAP && !E) return fail(c, RPM_ERR_INVALID_ARG, "E required");
+  if ((flags == RPM_GAMMA_FULL_MAP || flags == RPM_GAMMA_PROJECT) && !E)
+    return fail(c, RPM_ERR_INVALID_ARG, "E required");
   if (in == out) return fail(c, RPM_ERR_INVALID_ARG, "in and out alias");
+  if (flags == RPM_GAMMA_PROJECT) {
+    // E - Gamma0 * ((-C0) : in) = E + Gamma0 * (C0 : in): the pass-A table of gp
+    c->launches += gamma_launches(c->g.nx, c->g.ny);
+    if (!ck(c, launch_apply_gamma(c->gp, in, out, c->spec, E, GM_FULL_MAP, c->st), "project"))
+      return RPM_ERR_CUDA;
+    return RPM_OK;
+  }
   Ops ops{c};
   if (!ops.gamma(in, out, E, flags)) return RPM_ERR_CUDA;
   return RPM_OK;
@@ -802,7 +837,7 @@ rpm_status rpm_solve(rpm_ctx* c, const double E[6], const float* eps0, float* ep
   long long launches_warm = 0;
   double pbytes_warm = 0.0;
   int f_warm = 0;
-  if (c->opt.warm_tol > 0 && !eps0) {
+  if (c->opt.warm_tol > 0 && (!eps0 || c->opt.warm_from_eps0)) {
     // stage 1: Algorithm 3 (basis up to warm_p_max), C0 at the geometric mean of the phases
     double lmin = 1e300, lmax = 0, mmin = 1e300, mmax = 0;
     for (const auto& ph : c->phases) {
@@ -822,7 +857,7 @@ rpm_status rpm_solve(rpm_ctx* c, const double E[6], const float* eps0, float* ep
     c->opt.max_iters = c->opt.warm_max_iters;
     float* stage = c->fields + 5 * c->fst;        // D[0]: free until the solve proper grows Z
     rpm_status s1 = ck(c, set_reference_medium(c, cw), "reference medium")
-                        ? solve_impl(c, E, nullptr, stage, nullptr, 0, &warm)
+                        ? solve_impl(c, E, eps0, stage, nullptr, 0, &warm)
                         : RPM_ERR_CUDA;
     c->opt = saved;
     if (!ck(c, set_reference_medium(c, c0_saved), "reference medium")) return RPM_ERR_CUDA;
@@ -886,7 +921,7 @@ rpm_status rpm_set_materials(rpm_ctx* c, int n_phases, const rpm_iso* phases, rp
   if (!(c0.mu > 0) || !(c0.lambda + 2 * c0.mu > 0))
     return fail(c, RPM_ERR_INVALID_ARG, "bad reference medium");
   c->phases.assign(phases, phases + n_phases);
-  c->g.n_phases = c->gb.n_phases = n_phases;
+  c->g.n_phases = c->gb.n_phases = c->gp.n_phases = n_phases;
   std::vector<float2> cm(256, make_float2(0.f, 0.f));
   for (int i = 0; i < n_phases; ++i)
     cm[i] = make_float2((float)phases[i].lambda, (float)phases[i].mu);

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "rpm.h"
+
 namespace rpm {
 
 constexpr int kMaxBasis = 256;   // largest unstable basis (projections run in chunks of 32)
@@ -70,5 +72,15 @@ cudaError_t launch_polarization_post(const GridDev& g, const float4* post, const
                                      const float* eps_b, float* out, cudaStream_t st);
 cudaError_t launch_newton(const double* sums, int p, const double* M, const double* z, double* c,
                           double* znext, double* res_out, double inv_norm, cudaStream_t st);
+
+// ---- context view for the learned warm start (rpm_api.cu) ----------------
+struct CellView {
+  int nx, ny, nz;
+  const uint8_t* phase;   // device [nz][ny][nx]
+  const rpm_iso* phases;  // host, n_phases entries
+  int n_phases;
+  cudaStream_t st;        // the context stream
+};
+bool ctx_cell_view(const rpm_ctx* c, CellView* v);
 
 }  // namespace rpm

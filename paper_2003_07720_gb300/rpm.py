@@ -33,6 +33,7 @@ RPM_SCHEME_POLARIZATION = 1
 RPM_GAMMA_FULL_MAP = 0
 RPM_GAMMA_LINEAR = 1
 RPM_GAMMA_RAW_TAU = 2
+RPM_GAMMA_PROJECT = 3
 
 
 class rpm_grid(ctypes.Structure):
@@ -51,7 +52,8 @@ class rpm_options(ctypes.Structure):
                 ("max_device_gb", ctypes.c_double), ("profile", ctypes.c_int),
                 ("scheme", ctypes.c_int), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
                 ("warm_tol", ctypes.c_double), ("warm_c0_scale", ctypes.c_double),
-                ("warm_max_iters", ctypes.c_int), ("warm_p_max", ctypes.c_int)]
+                ("warm_max_iters", ctypes.c_int), ("warm_p_max", ctypes.c_int),
+                ("warm_from_eps0", ctypes.c_int)]
 
 
 class rpm_solve_info(ctypes.Structure):

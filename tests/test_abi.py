@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 import __graft_entry__ as entry
@@ -69,3 +70,26 @@ def test_host_side_checks(L):
                       rpm.rpm_iso(1.0, 1.0), ctypes.byref(bad), None, ctypes.byref(h))
     assert st == rpm.RPM_ERR_INVALID_ARG
     assert L.rpm_status_string(5) == b"RPM_ERR_NOT_CONVERGED"
+
+
+def test_fno_host_side_checks(L):
+    import ctypes as ct
+    from paper_2003_07720_gb300 import fno
+    F = fno.lib()
+    assert set(fno.EXPORTS) <= _declared()
+    m, layers = 12, 4
+    assert fno.param_count(m, layers) == 256 + layers * (272 + 2 * (2 * m * m) * (2 * m) * 256)
+    assert fno.param_count(0, 1) == 0 and fno.param_count(13, 1) == 0
+    assert fno.param_count(4, 0) == 0 and fno.param_count(4, 9) == 0
+    h = ct.c_void_p()
+    for cfg in [(20, 4, 1, 1), (32, 17, 1, 1), (36, 4, 1, 1), (32, 4, 0, 1), (32, 4, 1, 0),
+                (136, 4, 1, 1), (24, 13, 1, 1)]:
+        st = F.rpm_fno_create(ct.byref(fno.rpm_fno_config(*cfg)), None, ct.byref(h))
+        assert st == 1 and not h.value, cfg
+    assert F.rpm_fno_create(None, None, ct.byref(h)) == 1
+    # layout round trip of the dictionary form
+    import microstructure as ms
+    p = ms.fno_params(3, 2, seed=1)
+    back = fno.unpack_params(fno.pack_params(p, 3, 2), 3, 2)
+    for k in p:
+        assert np.allclose(back[k], p[k], atol=1e-6), k
