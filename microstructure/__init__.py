@@ -301,8 +301,8 @@ def strain_direction(s: int) -> np.ndarray:
     return e / math.sqrt(float(np.sum(w * e * e)))
 
 
-def fno_params(modes: int, layers: int, seed: int = 0, width: int = 16, cin: int = 8,
-               cout: int = 6) -> dict:
+def fno_params(modes: int, layers: int, seed: int = 0, width: int = 16, cin: int = 2,
+               cout: int = 36) -> dict:
     """Random parameters of the spectral neural operator: dense maps
     N(0, 1 / fan_in), biases zero, spectral weights with real and imaginary
     parts uniform in [0, 1 / width^2); R{l} is complex [in][out][4 modes^3]."""

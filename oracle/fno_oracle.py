@@ -3,9 +3,14 @@
 
 Network (width W, L Fourier layers, m modes per axis), on a periodic N^3 grid:
 
-  v0       = P x + p                               (lift, per voxel; x has Cin channels)
+  v0       = P f + p                               (lift, per voxel; f: 2 voxel features)
   v_{l+1}  = act_l( A_l v_l + a_l + K_l v_l )       l = 0 .. L-1, act = GELU except the last
-  out      = Q v_L + q                             (projection, per voxel)
+  H        = Q v_L + q                             (36 channels per voxel: a 6 x 6 map)
+  out[o]   = sum_j H[o, j] E_j                     (strain for the macroscopic strain E)
+
+The output is linear in E, as the solution of the linear cell problem is:
+the network maps the microstructure to a localisation field H(x) and the
+strain for any E follows by one contraction.
 
 K_l is the truncated spectral convolution: forward transform of each channel
 restricted to the kept modes (kx in [0, m), ky, kz in {0..m-1} U {N-m..N-1}),
@@ -77,12 +82,13 @@ def inv_trunc(U, N, m, weighted=True):
     return np.einsum("...zyk,kx->...zyx", a, np.conj(Fx)).real
 
 
-def forward(params, x, modes: int, layers: int, keep=False):
-    """x [B, Cin, N, N, N] -> out [B, Cout, N, N, N] (and the saved activations)."""
-    N = x.shape[-1]
+def forward(params, f, E, modes: int, layers: int, keep=False):
+    """f [B, 2, N, N, N] voxel features, E [B, 6] -> out [B, 6, N, N, N]
+    (and the saved activations)."""
+    N = f.shape[-1]
     M2 = 2 * modes
-    v = np.einsum("oc,bc...->bo...", params["P"], x) + params["p"][None, :, None, None, None]
-    saved = {"x": x, "v": [v], "z": [], "V": []}
+    v = np.einsum("oc,bc...->bo...", params["P"], f) + params["p"][None, :, None, None, None]
+    saved = {"x": f, "v": [v], "z": [], "V": []}
     for l in range(layers):
         V = trunc_dft(v, modes).reshape(v.shape[0], v.shape[1], -1)          # [B, W, M]
         U = np.einsum("bim,iom->bom", V, params[f"R{l}"]).reshape(v.shape[0], -1, M2, M2, modes)
@@ -93,12 +99,14 @@ def forward(params, x, modes: int, layers: int, keep=False):
         saved["z"].append(z)
         saved["V"].append(V)
         saved["v"].append(v)
-    out = np.einsum("oc,bc...->bo...", params["Q"], v) + params["q"][None, :, None, None, None]
+    H = np.einsum("oc,bc...->bo...", params["Q"], v) + params["q"][None, :, None, None, None]
+    H = H.reshape((H.shape[0], 6, 6) + H.shape[2:])
+    out = np.einsum("boj...,bj->bo...", H, np.asarray(E, float))
     return (out, saved) if keep else out
 
 
-def loss(params, x, target, modes, layers):
-    out = forward(params, x, modes, layers)
+def loss(params, f, E, target, modes, layers):
+    out = forward(params, f, E, modes, layers)
     return float(np.mean((out - target) ** 2))
 
 
@@ -108,19 +116,21 @@ def _outer_sum(a, b):
     return np.einsum("bon,bcn->oc", a.reshape(B, a.shape[1], -1), b.reshape(B, b.shape[1], -1))
 
 
-def backward(params, x, target, modes: int, layers: int):
+def backward(params, f, E, target, modes: int, layers: int):
     """Loss and gradients of every parameter (complex R: dL/dRe + i dL/dIm)."""
-    out, s = forward(params, x, modes, layers, keep=True)
-    N = x.shape[-1]
-    B = x.shape[0]
+    out, s = forward(params, f, E, modes, layers, keep=True)
+    N = f.shape[-1]
+    B = f.shape[0]
     M2 = 2 * modes
     nel = out.size
     g = {}
     d_out = 2.0 * (out - target) / nel
     vL = s["v"][-1]
-    g["Q"] = _outer_sum(d_out, vL)
-    g["q"] = d_out.sum(axis=(0, 2, 3, 4))
-    dv = np.einsum("oc,bo...->bc...", params["Q"], d_out)
+    dH = np.einsum("bo...,bj->boj...", d_out, np.asarray(E, float))
+    dH = dH.reshape((B, 36) + dH.shape[3:])
+    g["Q"] = _outer_sum(dH, vL)
+    g["q"] = dH.sum(axis=(0, 2, 3, 4))
+    dv = np.einsum("oc,bo...->bc...", params["Q"], dH)
     for l in reversed(range(layers)):
         z = s["z"][l]
         v = s["v"][l]
@@ -137,7 +147,7 @@ def backward(params, x, target, modes: int, layers: int):
         dV = np.einsum("bom,iom->bim", dU, np.conj(params[f"R{l}"]))
         dv_prev = dv_prev + inv_trunc(dV.reshape(B, -1, M2, M2, modes), N, modes, weighted=False)
         dv = dv_prev
-    g["P"] = _outer_sum(dv, x)
+    g["P"] = _outer_sum(dv, f)
     g["p"] = dv.sum(axis=(0, 2, 3, 4))
     return float(np.mean((out - target) ** 2)), g
 

@@ -59,14 +59,26 @@ def test_zero_spectral_weights_reduce_to_pointwise_network():
     p = fno_params(m, L, seed=4, width=5)
     for l in range(L):
         p[f"R{l}"][:] = 0
-    x = _rng(5).standard_normal((1, 8, N, N, N))
-    out = fo.forward(p, x, m, L)
+    x = _rng(5).standard_normal((1, 2, N, N, N))
+    E = _rng(15).standard_normal((1, 6))
+    out = fo.forward(p, x, E, m, L)
     h = np.einsum("oc,c...->o...", p["P"], x[0]) + p["p"][:, None, None, None]
     h = np.einsum("oc,c...->o...", p["A0"], h) + p["a0"][:, None, None, None]
     h = 0.5 * h * (1 + np.tanh(np.sqrt(2 / np.pi) * (h + 0.044715 * h ** 3)))
     h = np.einsum("oc,c...->o...", p["A1"], h) + p["a1"][:, None, None, None]
-    ref = np.einsum("oc,c...->o...", p["Q"], h) + p["q"][:, None, None, None]
+    H = np.einsum("oc,c...->o...", p["Q"], h) + p["q"][:, None, None, None]
+    ref = sum(E[0, j] * H[j::6] for j in range(6))       # H channel 6 o + j, out_o = H_oj E_j
     assert np.allclose(out[0], ref, atol=1e-12)
+
+
+def test_output_is_linear_in_the_macroscopic_strain():
+    N, m, L = 8, 2, 2
+    p = fno_params(m, L, seed=16, width=4)
+    f = _rng(17).standard_normal((1, 2, N, N, N))
+    E1, E2 = _rng(18).standard_normal((1, 6)), _rng(19).standard_normal((1, 6))
+    a = fo.forward(p, f, 2.0 * E1 - 3.0 * E2, m, L)
+    b = 2.0 * fo.forward(p, f, E1, m, L) - 3.0 * fo.forward(p, f, E2, m, L)
+    assert np.allclose(a, b, atol=1e-12)
 
 
 def test_gelu_derivative_matches_difference_quotient():
@@ -86,9 +98,10 @@ def test_gradient_matches_central_differences(name):
     for l in range(L):   # larger spectral weights so the branch matters
         p[f"R{l}"] *= 20.0
         p[f"a{l}"] = 0.1 * _rng(7 + l).standard_normal(3)
-    x = _rng(9).standard_normal((B, 8, N, N, N))
+    x = _rng(9).standard_normal((B, 2, N, N, N))
+    E = _rng(20).standard_normal((B, 6))
     t = _rng(10).standard_normal((B, 6, N, N, N))
-    _, g = fo.backward(p, x, t, m, L)
+    _, g = fo.backward(p, x, E, t, m, L)
     a = p[name]
     rng = _rng(11)
     idx = [tuple(rng.integers(0, s) for s in a.shape) for _ in range(4)]
@@ -98,9 +111,9 @@ def test_gradient_matches_central_differences(name):
         for unit in parts:
             old = a[ix]
             a[ix] = old + h * unit
-            lp = fo.loss(p, x, t, m, L)
+            lp = fo.loss(p, x, E, t, m, L)
             a[ix] = old - h * unit
-            lm = fo.loss(p, x, t, m, L)
+            lm = fo.loss(p, x, E, t, m, L)
             a[ix] = old
             fd = (lp - lm) / (2 * h)
             got = g[name][ix].real if unit == 1.0 else g[name][ix].imag
@@ -112,9 +125,10 @@ def test_input_gradient_matches_central_differences():
     # voxel input (the first-layer input gradient is g["P"]'s factor)
     N, m, L = 8, 2, 2
     p = fno_params(m, L, seed=12, width=3)
-    x = _rng(13).standard_normal((1, 8, N, N, N))
+    x = _rng(13).standard_normal((1, 2, N, N, N))
+    E = _rng(21).standard_normal((1, 6))
     t = _rng(14).standard_normal((1, 6, N, N, N))
-    _, g = fo.backward(p, x, t, m, L)
+    _, g = fo.backward(p, x, E, t, m, L)
     # gP[o][c] = sum_vox dv0[o] x[c]: perturbing x scaled by (1 + s) along
     # channel c changes the loss by s * sum_o P[o][c] gP-contributions; use
     # the exact identity d/ds L(P with column c scaled) = sum_o gP[o][c] P[o][c]
@@ -122,9 +136,9 @@ def test_input_gradient_matches_central_differences():
     h = 1e-6
     pp = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in p.items()}
     pp["P"][:, c] *= 1 + h
-    lp = fo.loss(pp, x, t, m, L)
+    lp = fo.loss(pp, x, E, t, m, L)
     pp["P"][:, c] = p["P"][:, c] * (1 - h)
-    lm = fo.loss(pp, x, t, m, L)
+    lm = fo.loss(pp, x, E, t, m, L)
     fd = (lp - lm) / (2 * h)
     assert abs(fd - np.sum(g["P"][:, c] * p["P"][:, c])) < 1e-7 * max(1, abs(fd))
 
