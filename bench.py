@@ -521,6 +521,125 @@ def run_study_batch(args):
     print(json.dumps(out), flush=True)
 
 
+def fno_flops_per_sample(n: int, m: int, layers: int, width: int = 16) -> dict:
+    """Algorithmic FLOPs of one sample through the spectral neural operator
+    (truncated DFT stages as sums over N points per kept frequency; a real x
+    complex term is 4 flops, a complex multiply-add 8): forward, and forward
+    plus backward (the backward repeats the forward transform of dz, the
+    spectral mixing twice (dV and the R gradient), the inverse transforms and
+    the pointwise maps twice)."""
+    W = width
+    per_ch = 4 * m * n ** 3 + 16 * m * m * n * n + 32 * m ** 3 * n      # x, y, z forward
+    inv_ch = 32 * m ** 3 * n + 16 * m * m * n * n + 4 * m * n ** 3      # z, y, x inverse
+    mix = 32 * m ** 3 * W * W
+    pw = 2 * n ** 3 * W * W
+    fwd_layer = W * (per_ch + inv_ch) + mix + pw
+    bwd_layer = W * (per_ch + inv_ch) + 2 * mix + 2 * pw + 2 * n ** 3 * W * W   # + gA tiles
+    head = 2 * n ** 3 * (36 * W + 36)
+    return {"forward": layers * fwd_layer + head,
+            "train": layers * (fwd_layer + bwd_layer) + 3 * head}
+
+
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+
+
+def run_fno_kernel(args):
+    """Time one loss-and-gradient pass of the spectral neural operator (64^3,
+    12 modes, 4 layers, width 16, batch 8) on random inputs: `--kernel fno`.
+    Prints one JSON line with its FP32-ALU roofline."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as entry
+    entry.build()
+    from paper_2003_07720_gb300 import fno
+    n, m, L, B = args.fno_n, 12, 4, args.fno_batch
+    g = torch.Generator(device="cuda").manual_seed(0)
+    feat = torch.randn((B, 2, n, n, n), device="cuda", generator=g)
+    tgt = torch.randn((B, 6, n, n, n), device="cuda", generator=g)
+    E = np.stack([ms.strain_direction(i) for i in range(B)])
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    with fno.Fno(n, m, L, max_batch=B, stream=stream) as net:
+        net.set_params(ms.fno_params(m, L, seed=0))
+        for _ in range(args.warmup):
+            net.loss_grad(feat, E, tgt)
+        ts = []
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            net.loss_grad(feat, E, tgt)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+    t = statistics.median(ts) / 1e3
+    fl = fno_flops_per_sample(n, m, L)
+    ach = fl["train"] * B / t / 1e12
+    print(json.dumps({"kernel": "fno_loss_grad", "grid": [n, n, n], "batch": B, "modes": m,
+                      "layers": L, "median_ms": round(t * 1e3, 4),
+                      "all_ms": [round(v, 4) for v in ts],
+                      "roofline": {"bound": "alu", "achieved": round(ach, 2),
+                                   "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
+                                   "frac": round(ach / FP32_PEAK_TFLOPS, 4),
+                                   "flops_per_launch_group": fl["train"] * B}}), flush=True)
+
+
+def run_study_fno(args):
+    """NEXT-2 measurement: train the spectral neural operator on solver
+    solutions of cell_fno_member cells (64^3), then compare, on held-out
+    cells at 64^3 and 128^3, the solve from eps0 = E, from the Algorithm 3
+    warm-start stage, from the learned guess and from the learned guess
+    followed by the stage.  Prints one JSON line."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as entry
+    entry.build()
+    from paper_2003_07720_gb300 import fno, fno_train
+    n, m, L, B = args.fno_n, 12, 4, args.fno_batch
+    out = {"study": "fno", "grid": n, "modes": m, "layers": L, "width": 16, "batch": B}
+    seeds = list(range(1000, 1000 + args.fno_train))
+    data = fno_train.make_dataset(n, seeds)
+    out["dataset"] = {"cells": len(seeds), "solve_seconds": round(data.solve_s, 2),
+                      "converged": int(data.converged.sum()), "train_samples": len(data.seeds)}
+    net = fno.Fno(n, m, L, max_batch=B)
+    net.set_params(ms.fno_params(m, L, seed=0))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = fno_train.train(net, data, args.fno_epochs, B, lr=args.fno_lr)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    out["training"] = {"epochs": args.fno_epochs, "seconds": round(t_train, 2), "lr": args.fno_lr,
+                       "samples_per_s": round(args.fno_epochs * (len(data.seeds) // B) * B
+                                              / t_train, 1),
+                       "loss_per_epoch": [float("%.5g" % v) for v in hist],
+                       "target_mean_square": float((data.target ** 2).mean().item())}
+    del data
+    torch.cuda.empty_cache()
+    params = net.get_params()
+    net.close()
+    test = list(range(5000, 5000 + args.fno_test))
+    res = {}
+    for nn in (n, 2 * n):
+        with fno.Fno(nn, m, L, max_batch=1) as net2:
+            net2.set_params(params)
+            rows = fno_train.evaluate(net2, nn, test)
+        summ = {}
+        both = [r for r in rows if all(r[f]["converged"] for f in ("cold", "learned"))]
+        for form in ("cold", "alg3_stage", "learned", "learned_alg3_stage"):
+            ok = [r[form] for r in rows if r[form]["converged"]]
+            summ[form] = {"converged": len(ok),
+                          "median_F": float(np.median([r["F"] for r in ok])) if ok else None,
+                          "median_ms": float(np.median([r["ms"] + r["guess_ms"] for r in ok]))
+                          if ok else None,
+                          "F_on_cells_cold_and_learned_both_converge":
+                              int(sum(r[form]["F"] for r in both))}
+        res[str(nn)] = {"summary": summ, "rows": rows}
+    out["evaluation"] = res
+    if args.fno_save:
+        np.save(args.fno_save, params)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -536,20 +655,31 @@ def main():
                          "geometric mean)")
     ap.add_argument("--max-iters", type=int, default=0,
                     help="cap the solve (profiling captures only; the result is not converged)")
-    ap.add_argument("--study", default=None, choices=[None, "fibre2d", "batch"],
+    ap.add_argument("--fno-n", type=int, default=64)
+    ap.add_argument("--fno-train", type=int, default=2000)
+    ap.add_argument("--fno-test", type=int, default=20)
+    ap.add_argument("--fno-epochs", type=int, default=60)
+    ap.add_argument("--fno-batch", type=int, default=8)
+    ap.add_argument("--fno-lr", type=float, default=2e-3)
+    ap.add_argument("--fno-save", default="", help="write the trained parameters (.npy)")
+    ap.add_argument("--study", default=None, choices=[None, "fibre2d", "batch", "fno"],
                     help="run a study instead of the benchmark")
     ap.add_argument("--study-tol", type=float, default=1e-6)
     ap.add_argument("--grid", type=int, default=N, help="cube size for --kernel gamma "
                     "(the benchmark cell at 128, a laminate otherwise)")
     ap.add_argument("--batch-cells", type=int, default=16)
     ap.add_argument("--batch-workers", type=int, default=8)
-    ap.add_argument("--kernel", default=None, choices=[None, "gamma"],
+    ap.add_argument("--kernel", default=None, choices=[None, "gamma", "fno"],
                     help="time one kernel group alone instead of the solve")
     args = ap.parse_args()
     if args.study == "fibre2d":
         run_study_fibre2d(args)
     elif args.study == "batch":
         run_study_batch(args)
+    elif args.study == "fno":
+        run_study_fno(args)
+    elif args.kernel == "fno":
+        run_fno_kernel(args)
     elif args.kernel == "gamma":
         run_gamma_only(args)
     elif args.impl == "reference":

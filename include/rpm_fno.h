@@ -1,8 +1,8 @@
 /*
  * rpm_fno.h -- learned warm start for the cell problem: a 3D spectral neural
- * operator (truncated-Fourier layers) that maps a microstructure and a
- * macroscopic strain direction to a strain-field guess, trained on solutions
- * of the solver in rpm.h.
+ * operator (truncated-Fourier layers) that maps a microstructure to a
+ * localisation field, contracted with the macroscopic strain into a
+ * strain-field guess; trained on solutions of the solver in rpm.h.
  *
  * The paper has no counterpart: it solves every cell from eps0 = E (Sec. 3,
  * Algorithm 2).  This module only changes the starting field of
@@ -10,20 +10,21 @@
  * criterion, so the converged result does not depend on the network.
  *
  * Network (width W = 16, L layers, m kept modes per axis, periodic N^3 grid):
- *   v0      = P [f; E] + p                    per voxel; f = 2 voxel features,
- *                                             E = 6 strain components (broadcast)
+ *   v0      = P f + p                         per voxel; f = 2 voxel features
  *   v_{l+1} = act_l(A_l v_l + a_l + K_l v_l)  act = GELU (tanh form), none on
  *                                             the last layer
- *   out     = Q v_L + q                       6 strain components per voxel
+ *   H       = Q v_L + q                       36 channels: H[o][j] = channel 6 o + j
+ *   out[o]  = sum_j H[o][j] E_j               strain for macroscopic strain E
+ * The output is linear in E, as the solution of the (linear) cell problem
+ * is: the network maps the microstructure to a localisation field.
  * K_l: forward DFT of each channel restricted to the kept modes
  * (kx in [0, m); ky, kz in {0..m-1} U {N-m..N-1}: 4 m^3 modes), per-mode complex
  * channel mixing R_l[i][o], and the real inverse of that half spectrum
  * (1 / N^3, doubled for kx >= 1).  Loss: mean squared error over all outputs.
  *
  * Parameter vector (float32, rpm_fno_param_count floats), in this order:
- *   P [16][8]  (columns: feature 0, feature 1, E_11, E_22, E_33, E_23, E_13, E_12)
- *   p [16]  Q [6][16]  q [6]  (then zeros up to float 256)
- *   per layer l, from 256 + l * (272 + 2 * 2m * m * 2m * 256):
+ *   P [16][2]  p [16]  Q [36][16]  q [36]  (then zeros up to float 768)
+ *   per layer l, from 768 + l * (272 + 2 * 2m * m * 2m * 256):
  *     A_l [16][16] (out, in)  a_l [16]
  *     R_l [ky_i][kx][kz_i][i][o] complex (re, im), ky_i, kz_i in [0, 2m):
  *         index i < m is frequency i, index i >= m is frequency N - 2m + i.
@@ -36,7 +37,8 @@
  *   out     [B][6][N][N][N]  strain components in Voigt order (11,22,33,23,13,12),
  *                            tensor (not engineering) shears
  *   target  as out
- * E_dir: HOST float [B][6], the macroscopic strain direction of each sample.
+ * E_dir: HOST float [B][6], the macroscopic strain of each sample (Voigt
+ *        order, tensor shears).
  *
  * All calls are stream-ordered on the stream given at creation (NULL: legacy
  * stream); functions that return host values synchronise it.  Errors:
@@ -58,6 +60,7 @@ extern "C" {
 #define RPM_FNO_MAX_MODES 12
 #define RPM_FNO_MAX_LAYERS 8
 #define RPM_FNO_MAX_N 128
+#define RPM_FNO_MAX_BATCH 64
 
 typedef struct rpm_fno rpm_fno;
 
@@ -65,7 +68,7 @@ typedef struct {
   int n;          /* grid side N: 24..128, a multiple of 8, N >= 2 * modes */
   int modes;      /* m: 1..RPM_FNO_MAX_MODES */
   int layers;     /* L: 1..RPM_FNO_MAX_LAYERS */
-  int max_batch;  /* largest batch B of any call, >= 1 */
+  int max_batch;  /* largest batch B of any call, 1..RPM_FNO_MAX_BATCH */
 } rpm_fno_config;
 
 typedef struct {
@@ -107,10 +110,9 @@ rpm_status rpm_fno_train_step(rpm_fno* f, int batch, const float* feat, const fl
 rpm_status rpm_fno_features(const uint8_t* phase, long long n, int n_phases,
                             const rpm_iso* phases, float* feat, void* cuda_stream);
 
-/* Warm start of rpm_solve for the context's cell and macroscopic strain E:
- * features of the cell, network on the direction E / |E| (|E| the
- * Frobenius norm of the tensor), output scaled by |E|, then projected onto
- * the compatible fields of mean E (rpm_apply_gamma, RPM_GAMMA_PROJECT).
+/* Warm start of rpm_solve for the context's cell and macroscopic strain E
+ * (nonzero): features of the cell, the network, then the projection onto the
+ * compatible fields of mean E (rpm_apply_gamma, RPM_GAMMA_PROJECT).
  * eps0: DEVICE float [6][nz][ny][nx]; the context grid must be N^3.  Returns
  * after eps0 is written (synchronises both streams). */
 rpm_status rpm_fno_warm_start(rpm_fno* f, rpm_ctx* ctx, const double E[6], float* eps0);

@@ -38,24 +38,25 @@
 namespace {
 
 constexpr int W = RPM_FNO_WIDTH;   // channels of the hidden layers
-constexpr int CV = 2;              // voxel features
-constexpr int CE = 6;              // broadcast strain components
-constexpr int CIN = CV + CE;
-constexpr int COUT = 6;
+constexpr int CV = 2;              // voxel features (the network's input channels)
+constexpr int CE = 6;              // macroscopic strain components
+constexpr int COUT = 6;            // strain components out
+constexpr int NH = COUT * CE;      // localisation channels H[o][j]
 constexpr int kMaxModes = RPM_FNO_MAX_MODES;
 constexpr int kThreads = 256;
-constexpr int kHeader = 256;       // floats before layer 0 in the parameter vector
+constexpr int kHeader = 768;       // floats before layer 0 in the parameter vector
 constexpr int kLayerHead = W * W + W;
 constexpr int kPwBlocksMax = 4 * 152;
 constexpr float kGeluC = 0.7978845608028654f;   // sqrt(2 / pi)
 
 // offsets of the head parameters
 constexpr int kOffP = 0;
-constexpr int kOffQ = W * CIN + W;               // 144
-constexpr int kNeA = W * W + W;                  // gradient entries of (A, a)
-constexpr int kNeQ = COUT * W + COUT;            // (Q, q)
-constexpr int kNeP = W * CIN + W;                // (P, p)
+constexpr int kNeP = W * CV + W;                 // gradient entries of (P, p): 48
+constexpr int kOffQ = kNeP;
+constexpr int kNeA = W * W + W;                  // (A, a)
+constexpr int kNeQ = NH * W + NH;                // (Q, q): 612
 constexpr int kNeHead = kNeQ + 1;                // + squared-error sum
+static_assert(kOffQ + kNeQ <= kHeader, "head parameters overflow the header");
 
 size_t r_floats(int m) { return (size_t)2 * (2 * m * m) * (2 * m) * W * W; }
 size_t layer_floats(int m) { return kLayerHead + r_floats(m); }
@@ -412,9 +413,8 @@ struct TileAcc {
   }
 };
 
-// v0 = P [f; E_b] + p.   total = B N^3 voxels.
+// v0 = P f + p.   total = B N^3 voxels.
 __global__ void __launch_bounds__(kThreads) k_lift(const float* __restrict__ feat,
-                                                   const float* __restrict__ Ed,
                                                    const float* __restrict__ prm,
                                                    float* __restrict__ v0, long long N3, int B) {
   __shared__ float Ps[kNeP];
@@ -425,18 +425,12 @@ __global__ void __launch_bounds__(kThreads) k_lift(const float* __restrict__ fea
        gidx += (long long)gridDim.x * kThreads) {
     const int b = (int)(gidx / N3);
     const long long vox = gidx - b * N3;
-    float x[CIN];
-    x[0] = feat[((long long)b * CV + 0) * N3 + vox];
-    x[1] = feat[((long long)b * CV + 1) * N3 + vox];
+    const float f0 = feat[((long long)b * CV + 0) * N3 + vox];
+    const float f1 = feat[((long long)b * CV + 1) * N3 + vox];
 #pragma unroll
-    for (int e = 0; e < CE; ++e) x[CV + e] = Ed[b * CE + e];
-#pragma unroll 4
-    for (int o = 0; o < W; ++o) {
-      float s = Ps[W * CIN + o];
-#pragma unroll
-      for (int c = 0; c < CIN; ++c) s = fmaf(Ps[o * CIN + c], x[c], s);
-      v0[((long long)b * W + o) * N3 + vox] = s;
-    }
+    for (int o = 0; o < W; ++o)
+      v0[((long long)b * W + o) * N3 + vox] =
+          fmaf(Ps[o * CV + 1], f1, fmaf(Ps[o * CV], f0, Ps[W * CV + o]));
   }
 }
 
@@ -446,15 +440,14 @@ __global__ void __launch_bounds__(kThreads) k_lift(const float* __restrict__ fea
   for (long long base = (long long)blockIdx.x * kThreads; base < (total);              \
        base += (long long)gridDim.x * kThreads)
 
-// Gradient of the lift: gP = sum dv0 [f; E_b]^T, gp = sum dv0.
+// Gradient of the lift: gP = sum dv0 f^T, gp = sum dv0.
 __global__ void __launch_bounds__(kThreads) k_lift_bwd(const float* __restrict__ dv0,
                                                        const float* __restrict__ feat,
-                                                       const float* __restrict__ Ed,
                                                        float* __restrict__ part, long long N3,
                                                        int B) {
-  using Acc = TileAcc<W, CIN>;
+  using Acc = TileAcc<W, CV>;
   __shared__ float sL[W * Acc::LD];
-  __shared__ float sR[CIN * Acc::LD];
+  __shared__ float sR[CV * Acc::LD];
   Acc acc;
   acc.init();
   const long long total = N3 * B;
@@ -466,15 +459,13 @@ __global__ void __launch_bounds__(kThreads) k_lift_bwd(const float* __restrict__
       const long long vox = gidx - b * N3;
 #pragma unroll
       for (int o = 0; o < W; ++o) sL[o * Acc::LD + t] = dv0[((long long)b * W + o) * N3 + vox];
-      sR[0 * Acc::LD + t] = feat[((long long)b * CV + 0) * N3 + vox];
-      sR[1 * Acc::LD + t] = feat[((long long)b * CV + 1) * N3 + vox];
 #pragma unroll
-      for (int e = 0; e < CE; ++e) sR[(CV + e) * Acc::LD + t] = Ed[b * CE + e];
+      for (int c = 0; c < CV; ++c) sR[c * Acc::LD + t] = feat[((long long)b * CV + c) * N3 + vox];
     } else {
 #pragma unroll
       for (int o = 0; o < W; ++o) sL[o * Acc::LD + t] = 0.f;
 #pragma unroll
-      for (int c = 0; c < CIN; ++c) sR[c * Acc::LD + t] = 0.f;
+      for (int c = 0; c < CV; ++c) sR[c * Acc::LD + t] = 0.f;
     }
     __syncthreads();
     acc.step(sL, sR);
@@ -540,21 +531,43 @@ __global__ void __launch_bounds__(kThreads) k_bwd_pw(const float* __restrict__ d
   acc.store(part + (long long)blockIdx.x * Acc::NE);
 }
 
-// Projection out = oscale (Q v + q); with a target: d = 2 (out - t) / nel,
-// dvL = Q^T d, partials of gQ = sum d v^T, gq = sum d and of sum (out - t)^2.
+// Shared memory of k_head (floats): the two tiles, then per sample the
+// contracted maps QE_b[o][c] (c < W) and qE_b[o] (c = W), then E.
+size_t head_smem(int B) {
+  return ((size_t)(NH + W) * (kThreads + 1) + (size_t)B * COUT * (W + 1) + (size_t)B * CE) * 4;
+}
+
+// Localisation head: H = Q v + q (36 channels, channel 6 o + j = H[o][j]) and
+// out[o] = sum_j H[o][j] E_bj, computed through the per-sample contracted map
+// QE_b = sum_j Q[6 o + j] E_bj.  With a target: d = 2 (out - t) / nel,
+// dH[o][j] = d[o] E_bj, dvL = Q^T dH = QE_b^T d, and partials of
+// gQ = sum dH v^T, gq = sum dH and of sum (out - t)^2.
 __global__ void __launch_bounds__(kThreads) k_head(const float* __restrict__ v,
                                                    const float* __restrict__ prm,
+                                                   const float* __restrict__ Ed,
                                                    const float* __restrict__ target,
                                                    float* __restrict__ out,
                                                    float* __restrict__ dv,
                                                    float* __restrict__ part, long long N3, int B,
-                                                   float oscale, float inv_nel) {
-  using Acc = TileAcc<COUT, W>;
-  __shared__ float sL[COUT * Acc::LD];
-  __shared__ float sR[W * Acc::LD];
-  __shared__ float Qs[kNeQ];
+                                                   float inv_nel) {
+  using Acc = TileAcc<NH, W>;
+  extern __shared__ float4 smem4[];
+  float* sL = (float*)smem4;                 // [NH][LD]
+  float* sR = sL + NH * Acc::LD;             // [W][LD]
+  float* QE = sR + W * Acc::LD;              // [B][COUT][W + 1]
+  float* Es = QE + B * COUT * (W + 1);       // [B][CE]
   __shared__ float red[kThreads / 32];
-  for (int i = threadIdx.x; i < kNeQ; i += kThreads) Qs[i] = prm[kOffQ + i];
+  for (int i = threadIdx.x; i < B * CE; i += kThreads) Es[i] = Ed[i];
+  for (int i = threadIdx.x; i < B * COUT * (W + 1); i += kThreads) {
+    const int b = i / (COUT * (W + 1)), r = i - b * (COUT * (W + 1));
+    const int o = r / (W + 1), c = r - o * (W + 1);
+    float s = 0.f;
+    for (int j = 0; j < CE; ++j) {
+      const float q = c < W ? prm[kOffQ + (o * CE + j) * W + c] : prm[kOffQ + NH * W + o * CE + j];
+      s = fmaf(q, Ed[b * CE + j], s);
+    }
+    QE[i] = s;
+  }
   __syncthreads();
   Acc acc;
   acc.init();
@@ -567,16 +580,16 @@ __global__ void __launch_bounds__(kThreads) k_head(const float* __restrict__ v,
     if (have) {
       const int b = (int)(gidx / N3);
       const long long vox = gidx - b * N3;
+      const float* qe = QE + b * COUT * (W + 1);
       float x[W];
 #pragma unroll
       for (int c = 0; c < W; ++c) x[c] = v[((long long)b * W + c) * N3 + vox];
       float d[COUT];
 #pragma unroll
       for (int o = 0; o < COUT; ++o) {
-        float s = Qs[COUT * W + o];
+        float s = qe[o * (W + 1) + W];
 #pragma unroll
-        for (int c = 0; c < W; ++c) s = fmaf(Qs[o * W + c], x[c], s);
-        s *= oscale;
+        for (int c = 0; c < W; ++c) s = fmaf(qe[o * (W + 1) + c], x[c], s);
         const long long at = ((long long)b * COUT + o) * N3 + vox;
         if (out) out[at] = s;
         if (target) {
@@ -590,18 +603,20 @@ __global__ void __launch_bounds__(kThreads) k_head(const float* __restrict__ v,
         for (int c = 0; c < W; ++c) {
           float s = 0.f;
 #pragma unroll
-          for (int o = 0; o < COUT; ++o) s = fmaf(Qs[o * W + c], d[o], s);
+          for (int o = 0; o < COUT; ++o) s = fmaf(qe[o * (W + 1) + c], d[o], s);
           dv[((long long)b * W + c) * N3 + vox] = s;
           sR[c * Acc::LD + t] = x[c];
         }
 #pragma unroll
-        for (int o = 0; o < COUT; ++o) sL[o * Acc::LD + t] = d[o];
+        for (int o = 0; o < COUT; ++o)
+#pragma unroll
+          for (int j = 0; j < CE; ++j) sL[(o * CE + j) * Acc::LD + t] = d[o] * Es[b * CE + j];
       }
     }
     if (target) {
       if (!have) {
 #pragma unroll
-        for (int o = 0; o < COUT; ++o) sL[o * Acc::LD + t] = 0.f;
+        for (int k = 0; k < NH; ++k) sL[k * Acc::LD + t] = 0.f;
 #pragma unroll
         for (int c = 0; c < W; ++c) sR[c * Acc::LD + t] = 0.f;
       }
@@ -736,13 +751,12 @@ bool stage_E(rpm_fno* f, int B, const float* E_dir) {
 
 // Forward pass; keeps v_l and z_l.  out (optional), target (optional: then the
 // head also writes dv_L into dvb(0) and its partials).
-bool run_forward(rpm_fno* f, int B, const float* feat, const float* target, float* out,
-                 float oscale) {
+bool run_forward(rpm_fno* f, int B, const float* feat, const float* target, float* out) {
   const int N = f->N, m = f->m, L = f->L;
   const long long total = f->N3 * B;
   const int nb = pw_blocks(total);
   const float inv_n3 = 1.f / (float)f->N3;
-  k_lift<<<nb, kThreads, 0, f->st>>>(feat, f->Ed, f->params, f->v(0), f->N3, B);
+  k_lift<<<nb, kThreads, 0, f->st>>>(feat, f->params, f->v(0), f->N3, B);
   if (!fck(f, cudaGetLastError(), "lift")) return false;
   for (int l = 0; l < L; ++l) {
     k_xy_fwd<<<dim3(N, B), kThreads, xy_smem(N, m), f->st>>>(f->v(l), f->A2, f->tw, N, m);
@@ -755,11 +769,12 @@ bool run_forward(rpm_fno* f, int B, const float* feat, const float* target, floa
     if (!fck(f, cudaGetLastError(), "layer")) return false;
   }
   const float inv_nel = 1.f / (float)(total * COUT);
-  k_head<<<nb, kThreads, 0, f->st>>>(f->v(L), f->params, target, out, f->dvb(0), f->part,
-                                     f->N3, B, oscale, inv_nel);
+  k_head<<<nb, kThreads, head_smem(B), f->st>>>(f->v(L), f->params, f->Ed, target, out,
+                                                 f->dvb(0), f->part, f->N3, B, inv_nel);
   if (!fck(f, cudaGetLastError(), "head")) return false;
   if (target) {
-    k_reduce<<<1, 128, 0, f->st>>>(f->part, nb, kNeHead, kNeQ, 1, f->grads + kOffQ, f->extra);
+    k_reduce<<<(kNeHead + 127) / 128, 128, 0, f->st>>>(f->part, nb, kNeHead, kNeQ, 1,
+                                                        f->grads + kOffQ, f->extra);
     if (!fck(f, cudaGetLastError(), "reduce head")) return false;
   }
   return true;
@@ -788,7 +803,7 @@ bool run_backward(rpm_fno* f, int B, const float* feat) {
     if (!fck(f, cudaGetLastError(), "layer backward")) return false;
     cur = 1 - cur;
   }
-  k_lift_bwd<<<nb, kThreads, 0, f->st>>>(f->dvb(cur), feat, f->Ed, f->part, f->N3, B);
+  k_lift_bwd<<<nb, kThreads, 0, f->st>>>(f->dvb(cur), feat, f->part, f->N3, B);
   k_reduce<<<(kNeP + 127) / 128, 128, 0, f->st>>>(f->part, nb, kNeP, kNeP, 0, f->grads + kOffP,
                                                   nullptr);
   return fck(f, cudaGetLastError(), "lift backward");
@@ -809,7 +824,8 @@ rpm_status rpm_fno_create(const rpm_fno_config* cfg, void* cuda_stream, rpm_fno*
   if (!cfg || !out) return RPM_ERR_INVALID_ARG;
   *out = nullptr;
   const int N = cfg->n, m = cfg->modes, L = cfg->layers, B = cfg->max_batch;
-  if (m < 1 || m > kMaxModes || L < 1 || L > RPM_FNO_MAX_LAYERS || B < 1 || N < 24 ||
+  if (m < 1 || m > kMaxModes || L < 1 || L > RPM_FNO_MAX_LAYERS || B < 1 ||
+      B > RPM_FNO_MAX_BATCH || N < 24 ||
       N > RPM_FNO_MAX_N || N % 8 != 0 || N < 2 * m)
     return RPM_ERR_INVALID_ARG;
   rpm_fno* f = new rpm_fno();
@@ -868,6 +884,7 @@ rpm_status rpm_fno_create(const rpm_fno_config* cfg, void* cuda_stream, rpm_fno*
       set_smem((const void*)k_spec_bwd, spec_smem(RPM_FNO_MAX_N, kMaxModes)) != cudaSuccess ||
       set_smem((const void*)k_inv_xy<false>, inv_smem(kMaxModes, 16)) != cudaSuccess ||
       set_smem((const void*)k_inv_xy<true>, inv_smem(kMaxModes, 16)) != cudaSuccess ||
+      set_smem((const void*)k_head, head_smem(RPM_FNO_MAX_BATCH)) != cudaSuccess ||
       cudaStreamSynchronize(f->st) != cudaSuccess) {
     cudaGetLastError();
     rpm_fno_destroy(f);
@@ -910,7 +927,7 @@ rpm_status rpm_fno_forward(rpm_fno* f, int batch, const float* feat, const float
                            float* out) {
   if (!valid_batch(f, batch) || !feat || !E_dir || !out)
     return ffail(f, RPM_ERR_INVALID_ARG, "bad forward arguments");
-  if (!stage_E(f, batch, E_dir) || !run_forward(f, batch, feat, nullptr, out, 1.f))
+  if (!stage_E(f, batch, E_dir) || !run_forward(f, batch, feat, nullptr, out))
     return RPM_ERR_CUDA;
   return RPM_OK;
 }
@@ -919,7 +936,7 @@ rpm_status rpm_fno_loss_grad(rpm_fno* f, int batch, const float* feat, const flo
                              const float* target, double* loss) {
   if (!valid_batch(f, batch) || !feat || !E_dir || !target)
     return ffail(f, RPM_ERR_INVALID_ARG, "bad loss_grad arguments");
-  if (!stage_E(f, batch, E_dir) || !run_forward(f, batch, feat, target, nullptr, 1.f) ||
+  if (!stage_E(f, batch, E_dir) || !run_forward(f, batch, feat, target, nullptr) ||
       !run_backward(f, batch, feat))
     return RPM_ERR_CUDA;
   if (loss) {
@@ -1008,8 +1025,8 @@ rpm_status rpm_fno_warm_start(rpm_fno* f, rpm_ctx* ctx, const double E[6], float
   if (features_on(cv.phase, f->N3, cv.n_phases, cv.phases, f->feat1, f->ftab, f->st) != RPM_OK)
     return ffail(f, RPM_ERR_CUDA, "features");
   float e[6];
-  for (int k = 0; k < 6; ++k) e[k] = (float)(E[k] / nrm);
-  if (!stage_E(f, 1, e) || !run_forward(f, 1, f->feat1, nullptr, f->out1, (float)nrm) ||
+  for (int k = 0; k < 6; ++k) e[k] = (float)E[k];   // the output is linear in E
+  if (!stage_E(f, 1, e) || !run_forward(f, 1, f->feat1, nullptr, f->out1) ||
       !fck(f, cudaStreamSynchronize(f->st), "sync"))
     return RPM_ERR_CUDA;
   const rpm_status s = rpm_apply_gamma(ctx, f->out1, E, eps0, RPM_GAMMA_PROJECT);

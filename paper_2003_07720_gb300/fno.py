@@ -16,9 +16,9 @@ import numpy as np
 from . import rpm
 
 WIDTH = 16
-CIN = 8
-COUT = 6
-HEADER = 256
+CIN = 2          # voxel features
+COUT = 36        # localisation channels H[o][j] (channel 6 o + j)
+HEADER = 768
 
 
 class rpm_fno_config(ctypes.Structure):

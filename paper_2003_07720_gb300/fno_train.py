@@ -2,7 +2,9 @@
 
 Data: cells of microstructure.cell_fno_member on an n^3 grid, each with its
 own strain direction (microstructure.strain_direction); the target is the
-strain field the solver (rpm_solve) returns for that cell and direction.
+fluctuation eps - E of the strain field the solver (rpm_solve) returns for
+that cell and direction (rpm_fno_warm_start projects the network output onto
+the compatible fields of mean E, so a fluctuation is all it needs).
 Inputs are the voxel features (rpm_fno_features) and the direction.
 
 Everything numerical runs in the CUDA library: the solves, the features, the
@@ -44,7 +46,7 @@ def make_dataset(n: int, seeds, options=None, stream=None) -> Dataset:
     target = torch.empty((S, 6, n, n, n), device="cuda")
     E = np.stack([ms.strain_direction(s) for s in seeds])
     conv = np.zeros(S, bool)
-    opts = options or rpm.rpm_default_options(warm_tol=1e-4, max_iters=3000)
+    opts = options or rpm.rpm_default_options(warm_tol=1e-4, max_iters=1000)
     first = ms.cell_fno_member(seeds[0], n)
     t0 = time.perf_counter()
     with rpm.Context(first, opts, stream=stream) as ctx:
@@ -55,10 +57,22 @@ def make_dataset(n: int, seeds, options=None, stream=None) -> Dataset:
                 rpm.rpm_set_materials(ctx.handle, _phase_list(cell), (cell.lam0, cell.mu0))
             st, info = ctx.solve(E[i], eps_out=target[i], raise_on_failure=False)
             conv[i] = info["converged"]
+            target[i] -= torch.tensor(E[i], dtype=torch.float32, device="cuda").view(6, 1, 1, 1)
             ph = torch.from_numpy(np.ascontiguousarray(cell.phase, np.uint8)).cuda()
             fno.features(ph, _phase_list(cell), feat[i], stream=stream)
     torch.cuda.synchronize()
-    return Dataset(n, list(seeds), feat, E, target, conv, time.perf_counter() - t0)
+    dt = time.perf_counter() - t0
+    # train only on solutions that met the stopping test (compacted in place
+    # by device copies, front to back)
+    keep = np.flatnonzero(conv)
+    if len(keep) < S:
+        for j, i in enumerate(keep):
+            if i != j:
+                feat[j].copy_(feat[i])
+                target[j].copy_(target[i])
+        feat, target = feat[:len(keep)], target[:len(keep)]
+        E = E[keep]
+    return Dataset(n, [seeds[i] for i in keep], feat, E, target, conv, dt)
 
 
 def train(net: "fno.Fno", data: Dataset, epochs: int, batch: int, lr: float = 2e-3,
@@ -71,20 +85,25 @@ def train(net: "fno.Fno", data: Dataset, epochs: int, batch: int, lr: float = 2e
     steps = epochs * (S // batch)
     hist = []
     k = 0
+    net.epoch_s = []
+    fb = torch.empty((batch,) + tuple(data.feat.shape[1:]), device="cuda")
+    tb = torch.empty((batch,) + tuple(data.target.shape[1:]), device="cuda")
     for ep in range(epochs):
+        te = time.perf_counter()
         order = rng.permutation(S)
         tot = 0.0
         nb = 0
         for j in range(0, S - batch + 1, batch):
-            idx = torch.from_numpy(order[j:j + batch]).cuda()
-            f = data.feat.index_select(0, idx)
-            t = data.target.index_select(0, idx)
+            for q, i in enumerate(order[j:j + batch]):    # gather by device copies
+                fb[q].copy_(data.feat[int(i)])
+                tb[q].copy_(data.target[int(i)])
             e = data.E[order[j:j + batch]]
             a = lr_final + 0.5 * (lr - lr_final) * (1 + np.cos(np.pi * k / max(steps - 1, 1)))
-            tot += net.train_step(f, e, t, lr=float(a))
+            tot += net.train_step(fb, e, tb, lr=float(a))
             nb += 1
             k += 1
         hist.append(tot / max(nb, 1))
+        net.epoch_s.append(time.perf_counter() - te)
         if log:
             log(f"epoch {ep}: loss {hist[-1]:.4e}")
     return hist

@@ -78,12 +78,12 @@ def test_fno_host_side_checks(L):
     F = fno.lib()
     assert set(fno.EXPORTS) <= _declared()
     m, layers = 12, 4
-    assert fno.param_count(m, layers) == 256 + layers * (272 + 2 * (2 * m * m) * (2 * m) * 256)
+    assert fno.param_count(m, layers) == 768 + layers * (272 + 2 * (2 * m * m) * (2 * m) * 256)
     assert fno.param_count(0, 1) == 0 and fno.param_count(13, 1) == 0
     assert fno.param_count(4, 0) == 0 and fno.param_count(4, 9) == 0
     h = ct.c_void_p()
     for cfg in [(20, 4, 1, 1), (32, 17, 1, 1), (36, 4, 1, 1), (32, 4, 0, 1), (32, 4, 1, 0),
-                (136, 4, 1, 1), (24, 13, 1, 1)]:
+                (136, 4, 1, 1), (24, 13, 1, 1), (32, 4, 1, 65)]:
         st = F.rpm_fno_create(ct.byref(fno.rpm_fno_config(*cfg)), None, ct.byref(h))
         assert st == 1 and not h.value, cfg
     assert F.rpm_fno_create(None, None, ct.byref(h)) == 1

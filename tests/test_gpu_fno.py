@@ -36,12 +36,6 @@ def _inputs(N, B, seed):
     return feat, E
 
 
-def _oracle_x(feat, E):
-    B, _, N = feat.shape[:3]
-    Eb = np.broadcast_to(E[:, :, None, None, None], (B, 6, N, N, N))
-    return np.concatenate([feat, Eb], axis=1)
-
-
 def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
 
@@ -52,7 +46,7 @@ def _params(m, L, seed, scale_r=8.0):
         p[f"R{l}"] *= scale_r          # make the spectral branch carry weight
         p[f"a{l}"] = 0.05 * np.random.Generator(np.random.PCG64(seed + l)).standard_normal(16)
     p["p"] = 0.1 * np.ones(16)
-    p["q"] = 0.01 * np.arange(6)
+    p["q"] = 0.01 * np.arange(36)
     return p
 
 
@@ -65,7 +59,7 @@ def _round32(p):
 def test_forward_matches_oracle(fno, N, m, L, B):
     p = _round32(_params(m, L, 100 + N))
     feat, E = _inputs(N, B, N)
-    ref = fo.forward(p, _oracle_x(feat, E), m, L)
+    ref = fo.forward(p, feat, E.astype(np.float32).astype(np.float64), m, L)
     out = torch.empty((B, 6, N, N, N), device="cuda")
     with fno.Fno(N, m, L, max_batch=B) as net:
         net.set_params(p)
@@ -82,7 +76,8 @@ def test_loss_and_every_gradient_match_oracle(fno):
     feat, E = _inputs(N, B, 3)
     rng = np.random.Generator(np.random.PCG64(4))
     target = rng.standard_normal((B, 6, N, N, N)).astype(np.float32).astype(np.float64)
-    loss_ref, g_ref = fo.backward(p, _oracle_x(feat, E), target, m, L)
+    E = E.astype(np.float32).astype(np.float64)
+    loss_ref, g_ref = fo.backward(p, feat, E, target, m, L)
     with fno.Fno(N, m, L, max_batch=B) as net:
         net.set_params(p)
         loss = net.loss_grad(_dev(feat), E, _dev(target))
@@ -175,8 +170,8 @@ def test_training_lowers_the_loss(fno):
     gradients in the same direction as the loss)."""
     N, m, L, B = 32, 4, 2, 2
     feat, E = _inputs(N, B, 13)
-    x = _oracle_x(feat, E)
-    target = np.tanh(x[:, :6] + x[:, 1:7])        # a smooth pointwise target
+    # a target linear in E with a pointwise localisation: eps_o = E_o (1 + tanh f0)
+    target = E[:, :, None, None, None] * (1.0 + np.tanh(feat[:, :1]))
     with fno.Fno(N, m, L, max_batch=B) as net:
         net.set_params(ms.fno_params(m, L, seed=14))
         f, t = _dev(feat), _dev(target)
@@ -203,3 +198,22 @@ def test_bad_arguments(fno):
             eps0 = torch.empty((6, 32, 32, 32), device="cuda")
             with pytest.raises(fno.FnoError):
                 net.warm_start(ctx, np.zeros(6), eps0)             # E = 0
+
+
+def test_warm_stage_from_uniform_eps0_equals_default_warm_form():
+    """warm_from_eps0 = 1 with eps0 = E everywhere follows exactly the
+    trajectory of the default warm form (which starts from E)."""
+    from paper_2003_07720_gb300 import rpm
+    N = 32
+    cell = ms.cell_fno_member(1004, N)
+    E = 0.01 * ms.strain_direction(4)
+    eps0 = torch.from_numpy(np.broadcast_to(E[:, None, None, None], (6, N, N, N))
+                            .astype(np.float32).copy()).cuda()
+    with rpm.Context(cell, rpm.rpm_default_options(warm_tol=1e-4)) as ctx:
+        _, a = ctx.solve(E)
+        rpm.rpm_set_options(ctx.handle, rpm.rpm_default_options(warm_tol=1e-4, warm_from_eps0=1))
+        _, b = ctx.solve(E, eps0=eps0)
+    assert a["converged"] and b["converged"]
+    assert (a["warm_iters"], a["iters"], a["gamma_applies"]) == (b["warm_iters"], b["iters"],
+                                                                 b["gamma_applies"])
+    assert a["mean_stress"] == b["mean_stress"]
