@@ -638,18 +638,36 @@ __global__ void __launch_bounds__(kThreads) k_head(const float* __restrict__ v,
 }
 
 // dst[e] = sum over blocks of part[blk][e] (float64, fixed order) for e < n_grad;
-// the entries after n_grad go to extra (float64).
-__global__ void k_reduce(const float* __restrict__ part, int nblk, int stride, int n_grad,
-                         int n_extra, float* __restrict__ dst, double* __restrict__ extra) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n_grad + n_extra) return;
+// the entries after n_grad go to extra (float64).  A block takes 32
+// consecutive entries (one per lane: coalesced rows); its 8 warps take every
+// 8th partial row, then warp 0 adds the 8 warp sums in order.
+constexpr int kRedWarps = 8;
+__global__ void __launch_bounds__(32 * kRedWarps) k_reduce(const float* __restrict__ part,
+                                                           int nblk, int stride, int n_grad,
+                                                           int n_extra, float* __restrict__ dst,
+                                                           double* __restrict__ extra) {
+  __shared__ double sm[kRedWarps][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int e = blockIdx.x * 32 + lane;
+  const int ne = n_grad + n_extra;
   double s = 0.0;
-  for (int k = 0; k < nblk; ++k) s += (double)part[(long long)k * stride + e];
-  if (e < n_grad)
-    dst[e] = (float)s;
-  else
-    extra[e - n_grad] = s;
+  if (e < ne) {
+#pragma unroll 4
+    for (int k = w; k < nblk; k += kRedWarps) s += (double)part[(long long)k * stride + e];
+  }
+  sm[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && e < ne) {
+    double t = 0.0;
+    for (int q = 0; q < kRedWarps; ++q) t += sm[q][lane];
+    if (e < n_grad)
+      dst[e] = (float)t;
+    else
+      extra[e - n_grad] = t;
+  }
 }
+
+int reduce_blocks(int ne) { return (ne + 31) / 32; }
 
 // Adam with bias correction and decoupled weight decay.
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m1,
@@ -773,8 +791,8 @@ bool run_forward(rpm_fno* f, int B, const float* feat, const float* target, floa
                                                  f->dvb(0), f->part, f->N3, B, inv_nel);
   if (!fck(f, cudaGetLastError(), "head")) return false;
   if (target) {
-    k_reduce<<<(kNeHead + 127) / 128, 128, 0, f->st>>>(f->part, nb, kNeHead, kNeQ, 1,
-                                                        f->grads + kOffQ, f->extra);
+    k_reduce<<<reduce_blocks(kNeHead), 32 * kRedWarps, 0, f->st>>>(f->part, nb, kNeHead, kNeQ, 1,
+                                                                   f->grads + kOffQ, f->extra);
     if (!fck(f, cudaGetLastError(), "reduce head")) return false;
   }
   return true;
@@ -792,8 +810,8 @@ bool run_backward(rpm_fno* f, int B, const float* feat) {
     float* prev = f->dvb(1 - cur);
     k_bwd_pw<<<nb, kThreads, 0, f->st>>>(f->dvb(cur), last ? nullptr : f->z(l), f->v(l),
                                          f->layer(l), dz, prev, f->part, f->N3, B, last);
-    k_reduce<<<(kNeA + 127) / 128, 128, 0, f->st>>>(f->part, nb, kNeA, kNeA, 0, f->glayer(l),
-                                                    nullptr);
+    k_reduce<<<reduce_blocks(kNeA), 32 * kRedWarps, 0, f->st>>>(f->part, nb, kNeA, kNeA, 0,
+                                                                f->glayer(l), nullptr);
     k_xy_fwd<<<dim3(N, B), kThreads, xy_smem(N, m), f->st>>>(dz, f->A2, f->tw, N, m);
     k_spec_bwd<<<f->ncol, kThreads, spec_smem(N, m), f->st>>>(
         f->A2, (const float2*)(f->layer(l) + kLayerHead), f->Vsl(l),
@@ -804,8 +822,8 @@ bool run_backward(rpm_fno* f, int B, const float* feat) {
     cur = 1 - cur;
   }
   k_lift_bwd<<<nb, kThreads, 0, f->st>>>(f->dvb(cur), feat, f->part, f->N3, B);
-  k_reduce<<<(kNeP + 127) / 128, 128, 0, f->st>>>(f->part, nb, kNeP, kNeP, 0, f->grads + kOffP,
-                                                  nullptr);
+  k_reduce<<<reduce_blocks(kNeP), 32 * kRedWarps, 0, f->st>>>(f->part, nb, kNeP, kNeP, 0,
+                                                               f->grads + kOffP, nullptr);
   return fck(f, cudaGetLastError(), "lift backward");
 }
 
