@@ -77,7 +77,10 @@ __device__ __forceinline__ float dot4(float4 a, float4 b) {
   return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
 }
 
-// acc[0] = sum w |x - xm|^2 (or sum w |x|^2 without xm), acc[1 + j] = sum w x . Y_j
+// acc[0] = sum w |x - xm|^2 and acc[1 + j] = sum w (x - xm) . Y_j; without xm,
+// sum w |x|^2 and sum w x . Y_j.  The difference is formed per element before
+// any product, so Z^T (xi - eps) keeps its accuracy when xi and eps agree to
+// many digits (near convergence).
 // Partial sums go to rows [0] (the norm) and [1 + row0 + j] of `partials`.
 template <int KMAX>
 __global__ void __launch_bounds__(kRedThreads) k_dots(const float4* __restrict__ x,
@@ -104,7 +107,7 @@ __global__ void __launch_bounds__(kRedThreads) k_dots(const float4* __restrict__
     acc[0] = fmaf(w, dot4(d, d), acc[0]);
 #pragma unroll
     for (int j = 0; j < KMAX; ++j) {
-      if (j < K) acc[1 + j] = fmaf(w, dot4(a, Y[j * ys4 + q]), acc[1 + j]);
+      if (j < K) acc[1 + j] = fmaf(w, dot4(d, Y[j * ys4 + q]), acc[1 + j]);
     }
   }
   block_store<KMAX + 1>(acc, K + 1, row0, partials, nblk);
@@ -393,25 +396,27 @@ cudaError_t launch_fill(float* f, const double E[6], long long n, cudaStream_t s
 // z+ = z + M (zeta - z);  c = z+ - zeta (so eps_next = xi + Z c);  z_next = z+
 // (z = Z^T eps of the current iterate; z_next = Z^T eps_next).
 // res_out = sqrt(sums[0]) * inv_norm.
+// Newton step of Eqs. 3.10-3.13 in reduced coordinates.  With
+// d = zeta - z = Z^T (xi - eps) (sums[1..p], formed from the difference field)
+// and M = (I - H)^-1, the new iterate eps+ = xi + Z (z+ - zeta) with
+// z+ = z + M d needs only c = z+ - zeta = (M - I) d.
 __global__ void k_newton(const double* __restrict__ sums, int p, const double* __restrict__ M,
-                         const double* __restrict__ z, double* __restrict__ c,
-                         double* __restrict__ znext, double* res_out, double inv_norm) {
+                         double* __restrict__ c, double* res_out, double inv_norm) {
   __shared__ double d[kMaxBasis];
-  for (int j = threadIdx.x; j < p; j += blockDim.x) d[j] = sums[1 + j] - z[j];
+  for (int j = threadIdx.x; j < p; j += blockDim.x) d[j] = sums[1 + j];
   __syncthreads();
   for (int j = threadIdx.x; j < p; j += blockDim.x) {
-    double zp = z[j];
-    for (int k = 0; k < p; ++k) zp += M[(size_t)j * p + k] * d[k];
-    c[j] = zp - sums[1 + j];
-    znext[j] = zp;
+    double s = -d[j];
+    for (int k = 0; k < p; ++k) s += M[(size_t)j * p + k] * d[k];
+    c[j] = s;
   }
   if (threadIdx.x == 0) res_out[0] = sqrt(sums[0]) * inv_norm;   // NaN stays NaN
 }
 
-cudaError_t launch_newton(const double* sums, int p, const double* M, const double* z, double* c,
-                          double* znext, double* res_out, double inv_norm, cudaStream_t st) {
+cudaError_t launch_newton(const double* sums, int p, const double* M, double* c, double* res_out,
+                          double inv_norm, cudaStream_t st) {
   if (p > kMaxBasis) return cudaErrorInvalidValue;
-  k_newton<<<1, 256, 0, st>>>(sums, p, M, z, c, znext, res_out, inv_norm);
+  k_newton<<<1, 256, 0, st>>>(sums, p, M, c, res_out, inv_norm);
   return cudaGetLastError();
 }
 

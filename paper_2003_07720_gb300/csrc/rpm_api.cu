@@ -30,11 +30,14 @@ namespace {
 constexpr int kPCap = kMaxBasis;      // largest basis the kernels accept
 // layout of the small float64 device array
 constexpr int kSums = 0;              // 1 + kPCap reduced sums
-constexpr int kZa = kSums + kPCap + 8;   // reduced coordinates z (two buffers)
-constexpr int kZb = kZa + kPCap;
-constexpr int kC = kZb + kPCap;       // Newton correction c
+constexpr int kC = kSums + kPCap + 8;   // Newton correction c
 constexpr int kRes = kC + kPCap;      // residual
 constexpr int kBatch = 4;             // steps between host reads while the basis is empty
+constexpr int kFields = 10;           // field buffers of a context (see rpm_ctx::fields)
+constexpr int kMaxRebase = 16;        // re-centrings of one solve (see solve_impl)
+// Basis growth is skipped while |xi^nu - xi^(nu-1)| < kGrowNoise |xi|: such a
+// difference is dominated by the float32 rounding of F (about 2e-7 |xi|).
+constexpr double kGrowNoise = 1e-5;
 constexpr int kM = kRes + 8;          // (I - H)^-1, kPCap x kPCap
 constexpr int kSmall = kM + kPCap * kPCap;
 
@@ -61,7 +64,7 @@ struct rpm_ctx {
   char* tables = nullptr;
   uint8_t* phase = nullptr;
   float2* spec = nullptr;
-  float* fields = nullptr;           // eps[2], xi[3], D[2], eps_b
+  float* fields = nullptr;           // eps[2], xi[3], D[2], eps_b, base, defect
   float* Z = nullptr;
   float* W = nullptr;
   double* partials = nullptr;
@@ -464,7 +467,7 @@ rpm_status rpm_create(const rpm_grid* grid, const uint8_t* phase, int phase_on_d
   c->nblk = std::max(dots_blocks_for(c->n), stress_blocks_for(c->n));
   const size_t fbytes = c->fst * sizeof(float);
   const size_t spec_bytes = (size_t)6 * nz * g.plane * sizeof(float2);
-  const size_t need = tab_bytes + align_up((size_t)c->n, 256) + spec_bytes + 8 * fbytes +
+  const size_t need = tab_bytes + align_up((size_t)c->n, 256) + spec_bytes + kFields * fbytes +
                       2 * (size_t)c->p_cap * fbytes + (size_t)(kPCap + 1) * c->nblk * 8 +
                       kSmall * 8;
   if (o.max_device_gb > 0 && (double)need > o.max_device_gb * 1e9) {
@@ -481,7 +484,7 @@ rpm_status rpm_create(const rpm_grid* grid, const uint8_t* phase, int phase_on_d
   if ((e = alloc((void**)&c->tables, tab_bytes)) != cudaSuccess ||
       (e = alloc((void**)&c->phase, align_up((size_t)c->n, 256))) != cudaSuccess ||
       (e = alloc((void**)&c->spec, spec_bytes)) != cudaSuccess ||
-      (e = alloc((void**)&c->fields, 8 * fbytes)) != cudaSuccess ||
+      (e = alloc((void**)&c->fields, kFields * fbytes)) != cudaSuccess ||
       (e = alloc((void**)&c->Z, (size_t)c->p_cap * fbytes)) != cudaSuccess ||
       (e = alloc((void**)&c->W, (size_t)c->p_cap * fbytes)) != cudaSuccess ||
       (e = alloc((void**)&c->partials, (size_t)(kPCap + 1) * c->nblk * 8)) != cudaSuccess ||
@@ -601,7 +604,6 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
   c->prof_used = 0;
   c->H.clear();
   std::vector<double> M;
-  int zcur = kZa, znext = kZb;
 
   if (!ck(c, cudaEventRecord(c->ev0, c->st), "event")) return RPM_ERR_CUDA;
   if (!ck(c, cudaMemsetAsync(ds, 0, kSmall * 8, c->st), "memset")) return RPM_ERR_CUDA;
@@ -616,12 +618,28 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
   if (!ops.fmap(eps_cur, xi[0], E, false)) return RPM_ERR_CUDA;
   nF = 1;
 
-  // residual, zeta = Z^T xi and the Newton correction for the current pair (eps, xi)
+  // Re-centring (defect correction).  After a stall the iterate is split as
+  // eps = base + y, base frozen; the map is then y -> r + F_u y with the
+  // defect r = F(base) - base, the same linear part (basis, H and M stay
+  // valid) and a fixed point at the same eps.  Float32 rounding then scales
+  // with |y| instead of |eps|, which removes the float32 floor the plain
+  // iteration meets on high-contrast cells.
+  float* base = c->fields + 8 * F;
+  float* defect = c->fields + 9 * F;
+  bool based = false;
+  int rebases = 0;
+  auto step_map = [&](const float* in, float* out) -> bool {
+    if (!based) return ops.fmap(in, out, E, false);
+    if (!ops.fmap(in, out, nullptr, true)) return false;
+    ++c->launches;
+    return ck(c, launch_axpby(out, 1.f, out, 1.f, defect, c->n, c->st), "defect");
+  };
+
+  // residual, zeta - z = Z^T (xi - eps) and the Newton correction for the current pair (eps, xi)
   auto eval = [&](double& r) -> bool {
     if (!ops.dots(xi[cur], eps_cur, c->Z, c->p, ds + kSums)) return false;
     c->launches += 1;
-    if (!ck(c, launch_newton(ds + kSums, c->p, ds + kM, ds + zcur, ds + kC, ds + znext, ds + kRes,
-                             inv_norm, c->st),
+    if (!ck(c, launch_newton(ds + kSums, c->p, ds + kM, ds + kC, ds + kRes, inv_norm, c->st),
             "newton"))
       return false;
     if (!ops.read_small(kRes, 1)) return false;
@@ -651,6 +669,9 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
     if (!ops.read_small(kSums, 1)) return false;
     const double T11 = std::sqrt(std::max(hs[kSums], 0.0));
     if (!(T11 > 0) || !std::isfinite(T11)) return true;
+    if (!ops.dots(xi[cur], nullptr, nullptr, 0, ds + kSums)) return false;
+    if (!ops.read_small(kSums, 1)) return false;
+    if (T11 < kGrowNoise * std::sqrt(std::max(hs[kSums], 0.0))) return true;   // rounding noise
     const double T12 = d10 / T11;
     (void)n11;
     if (!ck(c, (++c->launches, launch_axpby)(D[1], 1.f, D[1], (float)(-T12 / T11), D[0], c->n, c->st), "axpby"))
@@ -709,12 +730,6 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
                                c->st),
             "upload M"))
       return false;
-    // reduced coordinates of the current iterate for the new directions
-    if (!ops.dots(eps_cur, nullptr, c->Z + (size_t)p_old * F, p - p_old, ds + kSums)) return false;
-    if (!ck(c, cudaMemcpyAsync(ds + zcur + p_old, ds + kSums + 1, sizeof(double) * (p - p_old),
-                               cudaMemcpyDeviceToDevice, c->st),
-            "z"))
-      return false;
     return true;
   };
 
@@ -722,10 +737,34 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
     if (c->trace_res && k < c->trace_cap) c->trace_res[k] = rr;
     if (c->trace_p && k < c->trace_cap) c->trace_p[k] = c->p;
   };
+  // base += y; every stored xi -= y (coordinates of the new base); y = 0;
+  // the defect is the current xi.  The residual is unchanged.
+  auto rebase = [&]() -> bool {
+    c->launches += 1;
+    const bool ok_base = based ? ck(c, launch_axpby(base, 1.f, base, 1.f, eps_cur, c->n, c->st), "base")
+                               : ck(c, cudaMemcpyAsync(base, eps_cur, c->fsz * 4,
+                                                       cudaMemcpyDeviceToDevice, c->st), "base");
+    if (!ok_base) return false;
+    for (int k = 0; k < 3; ++k) {
+      if (xi[k] == eps_cur) continue;
+      ++c->launches;
+      if (!ck(c, launch_axpby(xi[k], 1.f, xi[k], -1.f, eps_cur, c->n, c->st), "shift")) return false;
+    }
+    if (!ck(c, cudaMemsetAsync(eps_cur, 0, c->fsz * 4, c->st), "zero") ||
+        !ck(c, cudaMemcpyAsync(defect, xi[cur], c->fsz * 4, cudaMemcpyDeviceToDevice, c->st),
+            "defect"))
+      return false;
+    based = true;
+    ++rebases;
+    return true;
+  };
+
   double r = 0;
   if (!eval(r)) return RPM_ERR_CUDA;
   trace(0, r);
   const double r0 = r;
+  double r_best = r;
+  int it_best = 0;
   inf.residual0 = r0;
   rpm_status status = RPM_OK;
   for (;;) {
@@ -754,10 +793,9 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
       } else {
         eps_next = (eps_cur == epsb[0]) ? epsb[1] : epsb[0];
         if (!ops.combine(eps_next, xi[cur], 1.f, c->Z, c->p, ds + kC, 1.f)) return RPM_ERR_CUDA;
-        std::swap(zcur, znext);
       }
       const int nxt = (cur + 1) % 3;
-      if (!ops.fmap(eps_next, xi[nxt], E, false)) return RPM_ERR_CUDA;
+      if (!step_map(eps_next, xi[nxt])) return RPM_ERR_CUDA;
       ++nF;
       ++it;
       ++nu;
@@ -769,6 +807,16 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
       if (b == batch - 1 && !eval(r)) return RPM_ERR_CUDA;
     }
     trace(it, r);
+    // stall: no halving of the residual in 3 (n_max + 1) steps -> re-centre
+    if (r < 0.5 * r_best) {
+      r_best = r;
+      it_best = it;
+    } else if (std::isfinite(r) && r > o.tol && it - it_best >= 3 * (o.n_max + 1) &&
+               rebases < kMaxRebase) {
+      if (!rebase() || !eval(r)) return RPM_ERR_CUDA;
+      r_best = r;
+      it_best = it;
+    }
     if (std::isfinite(r) && r > o.tol && r <= o.diverge_factor * r0 && nu > o.n_max) {
       if (c->p < std::min(o.p_max, c->p_cap) && hist == 3) {
         const int p_before = c->p;
@@ -779,6 +827,11 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
     }
   }
 
+  if (based) {   // eps = base + y
+    ++c->launches;
+    if (!ck(c, launch_axpby(base, 1.f, base, 1.f, eps_cur, c->n, c->st), "base")) return RPM_ERR_CUDA;
+    eps_cur = base;
+  }
   // outputs: eps, sigma = C : eps, <sigma>
   const size_t fb = c->fsz * sizeof(float);
   if (eps_out) {

@@ -70,8 +70,8 @@ cudaError_t launch_fill(float* f, const double E[6], long long n, cudaStream_t s
 // table post[r] = (lam_a, mu_a, lam_s, mu_s); s_a = lam_a tr(eps) I + 2 mu_a eps.
 cudaError_t launch_polarization_post(const GridDev& g, const float4* post, const float* eps,
                                      const float* eps_b, float* out, cudaStream_t st);
-cudaError_t launch_newton(const double* sums, int p, const double* M, const double* z, double* c,
-                          double* znext, double* res_out, double inv_norm, cudaStream_t st);
+cudaError_t launch_newton(const double* sums, int p, const double* M, double* c, double* res_out,
+                          double inv_norm, cudaStream_t st);
 
 // ---- context view for the learned warm start (rpm_api.cu) ----------------
 struct CellView {

@@ -60,5 +60,27 @@ def softincl128_warm():
         json.dump(out, f, indent=1)
 
 
+def stiff64():
+    """Oracle RPM solves of two stiff-inclusion cells of the learned-warm-start
+    test set (cell_fno_member 5012 and 5013 at 64^3: contrast 373 and 182),
+    cold start, E = 0.01 x strain_direction(seed), C0 = mean, p_max 20,
+    n_max 10, solved to tol 1e-8 so that a solve to 1e-6 can be compared."""
+    out = {}
+    for seed in (5012, 5013):
+        cell = ms.cell_fno_member(seed, 64)
+        prob = o.Problem.from_cell(cell)
+        E = 0.01 * ms.strain_direction(seed)
+        t0 = time.time()
+        r = o.rpm_solve(prob, E, o.Options(tol=1e-8, p_max=20, n_max=10, max_iters=1500))
+        r6 = next(i for i, v in enumerate(r.residuals) if v <= 1e-6)
+        out[str(seed)] = {"status": r.status, "iters": r.iters, "residual": r.residual,
+                          "iters_to_1e-6": r6, "E": list(map(float, E)),
+                          "mean_stress": list(map(float, r.mean_stress)),
+                          "seconds_one_core": time.time() - t0}
+    with open(os.path.join(HERE, "stiff64_oracle_solve.json"), "w") as f:
+        json.dump(out, f, indent=1)
+
+
 if __name__ == "__main__":
-    {"softincl128": softincl128, "softincl128_warm": softincl128_warm}[sys.argv[1]]()
+    {"softincl128": softincl128, "softincl128_warm": softincl128_warm,
+     "stiff64": stiff64}[sys.argv[1]]()
