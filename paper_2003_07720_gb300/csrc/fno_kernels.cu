@@ -76,10 +76,18 @@ __device__ __forceinline__ float gelu_grad(float x) {
 // Transforms
 // ---------------------------------------------------------------------------
 
-// shared-memory carve-up of k_xy_fwd (floats)
-__host__ __device__ inline size_t xy_plane_floats(int N) { return ((size_t)N * (N + 1) + 3) / 4 * 4; }
+// k_xy_fwd: channels are transformed G at a time (G planes in shared memory,
+// stored transposed [x][y] so that 4 consecutive rows at one x are one
+// 16-byte load).  Both stages are register-tiled truncated DFTs:
+//   x stage  X_c[y][kx] = sum_x v_c[y][x] Tx[x][kx]     tile 4 rows x 4 kx
+//   y stage  V_c[ky][kx] = sum_y X_c[y][kx] Ty[y][ky]    tile 4 ky x 2 kx
+// with twiddle tables Tx[x][kx] = exp(-2 pi i kx x / N) (kx padded to a
+// multiple of 4 with zeros) and Ty[y][ky_i] likewise for the kept ky.
+__host__ __device__ inline int xy_group(int N) { return N <= 64 ? 4 : 1; }
+__host__ __device__ inline int pad4(int v) { return (v + 3) / 4 * 4; }
 size_t xy_smem(int N, int m) {
-  return (xy_plane_floats(N) + 2 * ((size_t)N * m + (size_t)2 * m * m * W + N)) * 4;
+  const size_t G = xy_group(N), NP = N + 4, MP = pad4(m), KP = pad4(2 * m);
+  return (G * N * NP + 2 * (G * N * MP + (size_t)2 * m * m * W + N * MP + N * KP)) * 4;
 }
 
 // src [B][W][N][N][N] -> dst [B][N(z)][ncol][W] (complex); column = ky_i * m + kx.
@@ -88,48 +96,104 @@ __global__ void __launch_bounds__(kThreads) k_xy_fwd(const float* __restrict__ s
                                                      float2* __restrict__ dst,
                                                      const float2* __restrict__ twg, int N, int m) {
   extern __shared__ float4 smem4[];
-  const int P = N + 1;
+  const int G = xy_group(N), NP = N + 4, MP = pad4(m), KP = pad4(2 * m);
   const int ncol = 2 * m * m;
-  float* plane = (float*)smem4;
-  float2* X = (float2*)(plane + xy_plane_floats(N));   // [y][kx]
-  float2* acc = X + N * m;                             // [ncol][W]
-  float2* tw = acc + ncol * W;                         // [N]
+  float* planeT = (float*)smem4;                       // [G][x][NP]
+  float2* X = (float2*)(planeT + (size_t)G * N * NP);  // [G][y][MP]
+  float2* acc = X + (size_t)G * N * MP;                // [ncol][W]
+  float2* Tx = acc + ncol * W;                         // [x][MP]
+  float2* Ty = Tx + N * MP;                            // [y][KP]
   const int tid = threadIdx.x, z = blockIdx.x, b = blockIdx.y;
   const long long NN = (long long)N * N;
-  for (int i = tid; i < N; i += kThreads) tw[i] = twg[i];
-  for (int c = 0; c < W; ++c) {
-    const float* s = src + (((long long)b * W + c) * N + z) * NN;
-    __syncthreads();
-    for (int i = tid; i < N * N; i += kThreads) plane[(i / N) * P + i % N] = s[i];
-    __syncthreads();
-    for (int o = tid; o < N * m; o += kThreads) {
-      const int y = o / m, kx = o - (o / m) * m;
-      const float* row = plane + y * P;
-      float re = 0.f, im = 0.f;
-      int j = 0;
-      for (int x = 0; x < N; ++x) {
-        const float2 t = tw[j];
-        re = fmaf(row[x], t.x, re);
-        im = fmaf(row[x], t.y, im);
-        j += kx;
-        if (j >= N) j -= N;
-      }
-      X[o] = make_float2(re, im);
+  for (int i = tid; i < N * MP; i += kThreads) {
+    const int x = i / MP, k = i - x * MP;
+    Tx[i] = k < m ? twg[(k * x) % N] : make_float2(0.f, 0.f);
+  }
+  for (int i = tid; i < N * KP; i += kThreads) {
+    const int y = i / KP, k = i - y * KP;
+    Ty[i] = k < 2 * m ? twg[(kfreq(k, m, N) * y) % N] : make_float2(0.f, 0.f);
+  }
+  const int xq = N / 4, xk = MP / 4;          // x-stage tiles per channel: xq * xk
+  const int yk = KP / 4, yx = MP / 2;         // y-stage tiles per channel: yk * yx
+  for (int c0 = 0; c0 < W; c0 += G) {
+    __syncthreads();   // previous group's readers are done
+    for (int i = tid; i < G * N * N / 4; i += kThreads) {
+      const int g = i / (N * N / 4), r = i - g * (N * N / 4);
+      const int y = r / (N / 4), x = 4 * (r - y * (N / 4));
+      const float4 v = *reinterpret_cast<const float4*>(
+          src + (((long long)b * W + c0 + g) * N + z) * NN + (long long)y * N + x);
+      float* pt = planeT + (size_t)g * N * NP + y;
+      pt[(x + 0) * NP] = v.x;
+      pt[(x + 1) * NP] = v.y;
+      pt[(x + 2) * NP] = v.z;
+      pt[(x + 3) * NP] = v.w;
     }
     __syncthreads();
-    for (int o = tid; o < ncol; o += kThreads) {
-      const int kyi = o / m, kx = o - (o / m) * m;
-      const int ky = kfreq(kyi, m, N);
-      float re = 0.f, im = 0.f;
-      int j = 0;
-      for (int y = 0; y < N; ++y) {
-        const float2 v = X[y * m + kx], t = tw[j];
-        re += v.x * t.x - v.y * t.y;
-        im += v.x * t.y + v.y * t.x;
-        j += ky;
-        if (j >= N) j -= N;
+    for (int item = tid; item < G * xq * xk; item += kThreads) {
+      const int g = item / (xq * xk), r = item - g * (xq * xk);
+      const int yq = r / xk, kg = r - yq * xk;
+      const float* pv = planeT + (size_t)g * N * NP + 4 * yq;
+      const float2* pt = Tx + 4 * kg;
+      float re[4][4], im[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) re[a][k] = im[a][k] = 0.f;
+      for (int x = 0; x < N; ++x) {
+        const float4 v = *reinterpret_cast<const float4*>(pv + x * NP);
+        const float4 t01 = *reinterpret_cast<const float4*>(pt + x * MP);
+        const float4 t23 = *reinterpret_cast<const float4*>(pt + x * MP + 2);
+        const float vv[4] = {v.x, v.y, v.z, v.w};
+        const float tr[4] = {t01.x, t01.z, t23.x, t23.z};
+        const float ti[4] = {t01.y, t01.w, t23.y, t23.w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            re[a][k] = fmaf(vv[a], tr[k], re[a][k]);
+            im[a][k] = fmaf(vv[a], ti[k], im[a][k]);
+          }
       }
-      acc[o * W + c] = make_float2(re, im);
+      float2* px = X + ((size_t)g * N + 4 * yq) * MP + 4 * kg;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) px[a * MP + k] = make_float2(re[a][k], im[a][k]);
+    }
+    __syncthreads();
+    for (int item = tid; item < G * yk * yx; item += kThreads) {
+      const int g = item / (yk * yx), r = item - g * (yk * yx);
+      const int kq = r / yx, kp = r - kq * yx;
+      const float2* px = X + (size_t)g * N * MP + 2 * kp;
+      const float2* pt = Ty + 4 * kq;
+      float re[4][2], im[4][2];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int k = 0; k < 2; ++k) re[a][k] = im[a][k] = 0.f;
+      for (int y = 0; y < N; ++y) {
+        const float4 xv = *reinterpret_cast<const float4*>(px + y * MP);
+        const float4 t01 = *reinterpret_cast<const float4*>(pt + y * KP);
+        const float4 t23 = *reinterpret_cast<const float4*>(pt + y * KP + 2);
+        const float xr[2] = {xv.x, xv.z}, xi[2] = {xv.y, xv.w};
+        const float tr[4] = {t01.x, t01.z, t23.x, t23.z};
+        const float ti[4] = {t01.y, t01.w, t23.y, t23.w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            re[a][k] = fmaf(xr[k], tr[a], fmaf(-xi[k], ti[a], re[a][k]));
+            im[a][k] = fmaf(xr[k], ti[a], fmaf(xi[k], tr[a], im[a][k]));
+          }
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int kyi = 4 * kq + a, kx = 2 * kp + k;
+          if (kyi < 2 * m && kx < m)
+            acc[(kyi * m + kx) * W + c0 + g] = make_float2(re[a][k], im[a][k]);
+        }
     }
   }
   __syncthreads();
@@ -282,9 +346,57 @@ __global__ void __launch_bounds__(kThreads) k_spec_bwd(const float2* __restrict_
     if (k < m2) gr[k * W * W + tid] = g[k];
 }
 
+// k_inv_xy shared memory: S [ncol][W], Y [YC][m][W], TyT [2m][YC] (conjugate
+// roots of rows y0..y0+YC-1), Txw [m][N] (weighted roots), then A and a.
 size_t inv_smem(int m, int YC) {
-  return ((size_t)2 * m * m * W + (size_t)YC * m * W + RPM_FNO_MAX_N) * sizeof(float2) +
-         kLayerHead * sizeof(float);
+  return ((size_t)2 * m * m * W + (size_t)YC * m * W + (size_t)2 * m * YC +
+          (size_t)m * RPM_FNO_MAX_N) * sizeof(float2) + kLayerHead * sizeof(float);
+}
+
+// Pointwise end of k_inv_xy for the two voxels of a thread (at0, at1 =
+// offsets of their channel 0); each row of A is loaded once for both.
+template <bool BWD>
+__device__ __forceinline__ void inv_pointwise(const float (&u0)[W], const float (&u1)[W],
+                                              const float* Al, const float* __restrict__ vin,
+                                              float* __restrict__ zsave, float* __restrict__ vout,
+                                              long long at0, long long at1, long long N3,
+                                              int last) {
+  if (BWD) {
+#pragma unroll
+    for (int c = 0; c < W; ++c) {
+      vout[at0 + c * N3] += u0[c];
+      vout[at1 + c * N3] += u1[c];
+    }
+    return;
+  }
+  float v0[W], v1[W];
+#pragma unroll
+  for (int c = 0; c < W; ++c) {
+    v0[c] = vin[at0 + c * N3];
+    v1[c] = vin[at1 + c * N3];
+  }
+#pragma unroll
+  for (int oc = 0; oc < W; ++oc) {
+    float s0 = Al[W * W + oc] + u0[oc], s1 = Al[W * W + oc] + u1[oc];
+    const float4* ar = reinterpret_cast<const float4*>(Al + oc * W);
+#pragma unroll
+    for (int q = 0; q < W / 4; ++q) {
+      const float4 av = ar[q];
+      s0 = fmaf(av.x, v0[4 * q], fmaf(av.y, v0[4 * q + 1],
+                fmaf(av.z, v0[4 * q + 2], fmaf(av.w, v0[4 * q + 3], s0))));
+      s1 = fmaf(av.x, v1[4 * q], fmaf(av.y, v1[4 * q + 1],
+                fmaf(av.z, v1[4 * q + 2], fmaf(av.w, v1[4 * q + 3], s1))));
+    }
+    if (last) {
+      vout[at0 + oc * N3] = s0;
+      vout[at1 + oc * N3] = s1;
+    } else {
+      zsave[at0 + oc * N3] = s0;
+      zsave[at1 + oc * N3] = s1;
+      vout[at0 + oc * N3] = gelu(s0);
+      vout[at1 + oc * N3] = gelu(s1);
+    }
+  }
 }
 
 // Inverse y and x transforms of the mode columns of plane (z, b), rows
@@ -292,8 +404,11 @@ size_t inv_smem(int m, int YC) {
 //   BWD = false: z = A v + a + u (u weighted c(kx) / N^3); writes zsave (unless
 //                last) and vout = gelu(z) (z on the last layer).
 //   BWD = true : vout += u (unweighted).
+// y stage: Y[yy][kx][c] = sum_ky S[ky][kx][c] conj(root(ky y)), tile 4 rows x 2
+// channels; x stage: u_c(x) = sum_kx w(kx) Re(Y[yy][kx][c] exp(+i 2 pi kx x / N))
+// for the two voxels x and x + N/2 of a thread, then the pointwise map.
 template <bool BWD>
-__global__ void __launch_bounds__(kThreads) k_inv_xy(const float2* __restrict__ Bz,
+__global__ void __launch_bounds__(kThreads, 2) k_inv_xy(const float2* __restrict__ Bz,
                                                      const float2* __restrict__ twg,
                                                      const float* __restrict__ layer,
                                                      const float* __restrict__ vin,
@@ -301,70 +416,81 @@ __global__ void __launch_bounds__(kThreads) k_inv_xy(const float2* __restrict__ 
                                                      float* __restrict__ vout, int N, int m,
                                                      int YC, int last, float inv_n3) {
   extern __shared__ float4 smem4[];
-  const int ncol = 2 * m * m, tid = threadIdx.x;
+  const int ncol = 2 * m * m, tid = threadIdx.x, m2 = 2 * m;
   float2* S = (float2*)smem4;          // [ncol][W]
   float2* Y = S + ncol * W;            // [yy][kx][c]
-  float2* tw = Y + YC * m * W;         // [N]
-  float* Al = (float*)(tw + RPM_FNO_MAX_N);   // A [o][c], a [o]
+  float2* TyT = Y + YC * m * W;        // [ky_i][yy]
+  float2* Txw = TyT + m2 * YC;         // [kx][x]
+  float* Al = (float*)(Txw + m * RPM_FNO_MAX_N);   // A [o][c], a [o]
   const int y0 = blockIdx.x * YC, z = blockIdx.y, b = blockIdx.z;
   const long long N3 = (long long)N * N * N;
   const float2* src = Bz + ((long long)b * N + z) * ncol * W;
   for (int i = tid; i < ncol * W / 2; i += kThreads) ((float4*)S)[i] = ((const float4*)src)[i];
-  for (int i = tid; i < N; i += kThreads) tw[i] = twg[i];
+  for (int i = tid; i < m2 * YC; i += kThreads) {
+    const int k = i / YC, yy = i - k * YC;
+    TyT[i] = twg[(kfreq(k, m, N) * (y0 + yy)) % N];
+  }
+  for (int i = tid; i < m * N; i += kThreads) {
+    const int kx = i / N, x = i - kx * N;
+    const float w = BWD ? 1.f : (kx == 0 ? inv_n3 : 2.f * inv_n3);
+    const float2 t = twg[(kx * x) % N];
+    Txw[i] = make_float2(w * t.x, w * t.y);
+  }
   if (!BWD)
     for (int i = tid; i < kLayerHead; i += kThreads) Al[i] = layer[i];
   __syncthreads();
-  for (int o = tid; o < YC * m * W; o += kThreads) {
-    const int yy = o / (m * W), r = o - yy * (m * W), kx = r / W, c = r % W;
-    const int y = y0 + yy;
-    float re = 0.f, im = 0.f;
-    for (int kyi = 0; kyi < 2 * m; ++kyi) {
-      const int ky = kfreq(kyi, m, N);
-      const float2 s = S[(kyi * m + kx) * W + c], t = tw[(ky * y) % N];
-      re += s.x * t.x + s.y * t.y;   // s * conj(t)
-      im += s.y * t.x - s.x * t.y;
+  const int nyq = YC / 4;
+  for (int item = tid; item < nyq * m * (W / 2); item += kThreads) {
+    const int yq = item / (m * (W / 2)), r = item - yq * (m * (W / 2));
+    const int kx = r / (W / 2), cp = r - kx * (W / 2);
+    float re[4][2], im[4][2];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int k = 0; k < 2; ++k) re[a][k] = im[a][k] = 0.f;
+    for (int kyi = 0; kyi < m2; ++kyi) {
+      const float4 sv = *reinterpret_cast<const float4*>(S + (kyi * m + kx) * W + 2 * cp);
+      const float4 t01 = *reinterpret_cast<const float4*>(TyT + kyi * YC + 4 * yq);
+      const float4 t23 = *reinterpret_cast<const float4*>(TyT + kyi * YC + 4 * yq + 2);
+      const float sr[2] = {sv.x, sv.z}, si[2] = {sv.y, sv.w};
+      const float tr[4] = {t01.x, t01.z, t23.x, t23.z};
+      const float ti[4] = {t01.y, t01.w, t23.y, t23.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {   // s * conj(t)
+          re[a][k] = fmaf(sr[k], tr[a], fmaf(si[k], ti[a], re[a][k]));
+          im[a][k] = fmaf(si[k], tr[a], fmaf(-sr[k], ti[a], im[a][k]));
+        }
     }
-    Y[o] = make_float2(re, im);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+        Y[((4 * yq + a) * m + kx) * W + 2 * cp + k] = make_float2(re[a][k], im[a][k]);
   }
   __syncthreads();
-  for (int o = tid; o < YC * N; o += kThreads) {
-    const int yy = o / N, x = o - yy * N;
-    float u[W];
+  const int half = N / 2;
+  for (int item = tid; item < YC * half; item += kThreads) {
+    const int yy = item / half, x = item - yy * half;
+    float u0[W], u1[W];
 #pragma unroll
-    for (int c = 0; c < W; ++c) u[c] = 0.f;
-    int j = 0;
+    for (int c = 0; c < W; ++c) u0[c] = u1[c] = 0.f;
     for (int kx = 0; kx < m; ++kx) {
-      const float2 t = tw[j];
-      const float w = BWD ? 1.f : (kx == 0 ? inv_n3 : 2.f * inv_n3);
-      const float cr = w * t.x, ci = w * t.y;   // Re(Y e^{+i phi}) = Yr cos + Yi sin
-      const float2* yr = Y + (yy * m + kx) * W;
+      const float2 t0 = Txw[kx * N + x], t1 = Txw[kx * N + x + half];
+      const float4* yr = reinterpret_cast<const float4*>(Y + (yy * m + kx) * W);
 #pragma unroll
-      for (int c = 0; c < W; ++c) u[c] += yr[c].x * cr + yr[c].y * ci;
-      j += x;
-      if (j >= N) j -= N;
-    }
-    const long long vox = ((long long)z * N + y0 + yy) * N + x;
-    if (BWD) {
-#pragma unroll
-      for (int c = 0; c < W; ++c) vout[((long long)b * W + c) * N3 + vox] += u[c];
-    } else {
-      float v[W];
-#pragma unroll
-      for (int c = 0; c < W; ++c) v[c] = vin[((long long)b * W + c) * N3 + vox];
-#pragma unroll
-      for (int oc = 0; oc < W; ++oc) {
-        float s = Al[W * W + oc] + u[oc];
-#pragma unroll
-        for (int c = 0; c < W; ++c) s = fmaf(Al[oc * W + c], v[c], s);
-        const long long at = ((long long)b * W + oc) * N3 + vox;
-        if (last) {
-          vout[at] = s;
-        } else {
-          zsave[at] = s;
-          vout[at] = gelu(s);
-        }
+      for (int q = 0; q < W / 2; ++q) {
+        const float4 yv = yr[q];   // channels 2q, 2q + 1
+        u0[2 * q] = fmaf(yv.x, t0.x, fmaf(yv.y, t0.y, u0[2 * q]));
+        u0[2 * q + 1] = fmaf(yv.z, t0.x, fmaf(yv.w, t0.y, u0[2 * q + 1]));
+        u1[2 * q] = fmaf(yv.x, t1.x, fmaf(yv.y, t1.y, u1[2 * q]));
+        u1[2 * q + 1] = fmaf(yv.z, t1.x, fmaf(yv.w, t1.y, u1[2 * q + 1]));
       }
     }
+    const long long vox0 = ((long long)z * N + y0 + yy) * N + x;
+    inv_pointwise<BWD>(u0, u1, Al, vin, zsave, vout, (long long)b * W * N3 + vox0,
+                       (long long)b * W * N3 + vox0 + half, N3, last);
   }
 }
 
