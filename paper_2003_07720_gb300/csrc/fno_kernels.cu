@@ -77,9 +77,11 @@ __device__ __forceinline__ float gelu_grad(float x) {
 // ---------------------------------------------------------------------------
 
 // k_xy_fwd: channels are transformed G at a time (G planes in shared memory,
-// stored transposed [x][y] so that 4 consecutive rows at one x are one
-// 16-byte load).  Both stages are register-tiled truncated DFTs:
-//   x stage  X_c[y][kx] = sum_x v_c[y][x] Tx[x][kx]     tile 4 rows x 4 kx
+// row-major with a row stride of N + 4 floats, an odd number of 16-byte
+// units, so 16-byte reads of consecutive rows hit distinct banks).  Both
+// stages are register-tiled truncated DFTs:
+//   x stage  X_c[y][kx] = sum_x v_c[y][x] Tx[x][kx]     tile 4 rows (y, y + N/4,
+//                                                        y + N/2, y + 3N/4) x 4 kx
 //   y stage  V_c[ky][kx] = sum_y X_c[y][kx] Ty[y][ky]    tile 4 ky x 2 kx
 // with twiddle tables Tx[x][kx] = exp(-2 pi i kx x / N) (kx padded to a
 // multiple of 4 with zeros) and Ty[y][ky_i] likewise for the kept ky.
@@ -87,7 +89,7 @@ __host__ __device__ inline int xy_group(int N) { return N <= 64 ? 4 : 1; }
 __host__ __device__ inline int pad4(int v) { return (v + 3) / 4 * 4; }
 size_t xy_smem(int N, int m) {
   const size_t G = xy_group(N), NP = N + 4, MP = pad4(m), KP = pad4(2 * m);
-  return (G * N * NP + 2 * (G * N * MP + (size_t)2 * m * m * W + N * MP + N * KP)) * 4;
+  return (G * N * NP + 2 * (G * N * MP + N * MP + N * KP)) * 4;
 }
 
 // src [B][W][N][N][N] -> dst [B][N(z)][ncol][W] (complex); column = ky_i * m + kx.
@@ -98,13 +100,13 @@ __global__ void __launch_bounds__(kThreads) k_xy_fwd(const float* __restrict__ s
   extern __shared__ float4 smem4[];
   const int G = xy_group(N), NP = N + 4, MP = pad4(m), KP = pad4(2 * m);
   const int ncol = 2 * m * m;
-  float* planeT = (float*)smem4;                       // [G][x][NP]
+  float* planeT = (float*)smem4;                       // [G][y][NP]
   float2* X = (float2*)(planeT + (size_t)G * N * NP);  // [G][y][MP]
-  float2* acc = X + (size_t)G * N * MP;                // [ncol][W]
-  float2* Tx = acc + ncol * W;                         // [x][MP]
+  float2* Tx = X + (size_t)G * N * MP;                 // [x][MP]
   float2* Ty = Tx + N * MP;                            // [y][KP]
   const int tid = threadIdx.x, z = blockIdx.x, b = blockIdx.y;
   const long long NN = (long long)N * N;
+  float2* d = dst + ((long long)b * N + z) * ncol * W;
   for (int i = tid; i < N * MP; i += kThreads) {
     const int x = i / MP, k = i - x * MP;
     Tx[i] = k < m ? twg[(k * x) % N] : make_float2(0.f, 0.f);
@@ -120,45 +122,53 @@ __global__ void __launch_bounds__(kThreads) k_xy_fwd(const float* __restrict__ s
     for (int i = tid; i < G * N * N / 4; i += kThreads) {
       const int g = i / (N * N / 4), r = i - g * (N * N / 4);
       const int y = r / (N / 4), x = 4 * (r - y * (N / 4));
-      const float4 v = *reinterpret_cast<const float4*>(
-          src + (((long long)b * W + c0 + g) * N + z) * NN + (long long)y * N + x);
-      float* pt = planeT + (size_t)g * N * NP + y;
-      pt[(x + 0) * NP] = v.x;
-      pt[(x + 1) * NP] = v.y;
-      pt[(x + 2) * NP] = v.z;
-      pt[(x + 3) * NP] = v.w;
+      *reinterpret_cast<float4*>(planeT + ((size_t)g * N + y) * NP + x) =
+          *reinterpret_cast<const float4*>(
+              src + (((long long)b * W + c0 + g) * N + z) * NN + (long long)y * N + x);
     }
     __syncthreads();
     for (int item = tid; item < G * xq * xk; item += kThreads) {
       const int g = item / (xq * xk), r = item - g * (xq * xk);
       const int yq = r / xk, kg = r - yq * xk;
-      const float* pv = planeT + (size_t)g * N * NP + 4 * yq;
+      const float* pv = planeT + ((size_t)g * N + yq) * NP;   // rows yq + a N/4
       const float2* pt = Tx + 4 * kg;
+      const int rs = xq * NP;                                 // N/4 rows apart
       float re[4][4], im[4][4];
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int k = 0; k < 4; ++k) re[a][k] = im[a][k] = 0.f;
-      for (int x = 0; x < N; ++x) {
-        const float4 v = *reinterpret_cast<const float4*>(pv + x * NP);
-        const float4 t01 = *reinterpret_cast<const float4*>(pt + x * MP);
-        const float4 t23 = *reinterpret_cast<const float4*>(pt + x * MP + 2);
-        const float vv[4] = {v.x, v.y, v.z, v.w};
-        const float tr[4] = {t01.x, t01.z, t23.x, t23.z};
-        const float ti[4] = {t01.y, t01.w, t23.y, t23.w};
+      for (int x = 0; x < N; x += 4) {
+        float vv[4][4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 4; ++a) {
+          const float4 v = *reinterpret_cast<const float4*>(pv + a * rs + x);
+          vv[a][0] = v.x;
+          vv[a][1] = v.y;
+          vv[a][2] = v.z;
+          vv[a][3] = v.w;
+        }
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            re[a][k] = fmaf(vv[a], tr[k], re[a][k]);
-            im[a][k] = fmaf(vv[a], ti[k], im[a][k]);
-          }
+        for (int dx = 0; dx < 4; ++dx) {
+          const float4 t01 = *reinterpret_cast<const float4*>(pt + (x + dx) * MP);
+          const float4 t23 = *reinterpret_cast<const float4*>(pt + (x + dx) * MP + 2);
+          const float tr[4] = {t01.x, t01.z, t23.x, t23.z};
+          const float ti[4] = {t01.y, t01.w, t23.y, t23.w};
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              re[a][k] = fmaf(vv[a][dx], tr[k], re[a][k]);
+              im[a][k] = fmaf(vv[a][dx], ti[k], im[a][k]);
+            }
+        }
       }
-      float2* px = X + ((size_t)g * N + 4 * yq) * MP + 4 * kg;
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int a = 0; a < 4; ++a) {
+        float2* px = X + ((size_t)g * N + yq + a * xq) * MP + 4 * kg;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) px[a * MP + k] = make_float2(re[a][k], im[a][k]);
+        for (int k = 0; k < 4; ++k) px[k] = make_float2(re[a][k], im[a][k]);
+      }
     }
     __syncthreads();
     for (int item = tid; item < G * yk * yx; item += kThreads) {
@@ -192,13 +202,10 @@ __global__ void __launch_bounds__(kThreads) k_xy_fwd(const float* __restrict__ s
         for (int k = 0; k < 2; ++k) {
           const int kyi = 4 * kq + a, kx = 2 * kp + k;
           if (kyi < 2 * m && kx < m)
-            acc[(kyi * m + kx) * W + c0 + g] = make_float2(re[a][k], im[a][k]);
+            d[(kyi * m + kx) * W + c0 + g] = make_float2(re[a][k], im[a][k]);
         }
     }
   }
-  __syncthreads();
-  float2* d = dst + ((long long)b * N + z) * ncol * W;
-  for (int i = tid; i < ncol * W; i += kThreads) d[i] = acc[i];
 }
 
 size_t spec_smem(int N, int m) {
@@ -361,40 +368,46 @@ __device__ __forceinline__ void inv_pointwise(const float (&u0)[W], const float 
                                               float* __restrict__ zsave, float* __restrict__ vout,
                                               long long at0, long long at1, long long N3,
                                               int last) {
-  if (BWD) {
+  if constexpr (BWD) {   // all loads before any store: the stores cannot delay the loads
+    float g0[W], g1[W];
 #pragma unroll
     for (int c = 0; c < W; ++c) {
-      vout[at0 + c * N3] += u0[c];
-      vout[at1 + c * N3] += u1[c];
+      g0[c] = vout[at0 + c * N3];
+      g1[c] = vout[at1 + c * N3];
     }
-    return;
-  }
-  float v0[W], v1[W];
 #pragma unroll
-  for (int c = 0; c < W; ++c) {
-    v0[c] = vin[at0 + c * N3];
-    v1[c] = vin[at1 + c * N3];
-  }
-#pragma unroll
-  for (int oc = 0; oc < W; ++oc) {
-    float s0 = Al[W * W + oc] + u0[oc], s1 = Al[W * W + oc] + u1[oc];
-    const float4* ar = reinterpret_cast<const float4*>(Al + oc * W);
-#pragma unroll
-    for (int q = 0; q < W / 4; ++q) {
-      const float4 av = ar[q];
-      s0 = fmaf(av.x, v0[4 * q], fmaf(av.y, v0[4 * q + 1],
-                fmaf(av.z, v0[4 * q + 2], fmaf(av.w, v0[4 * q + 3], s0))));
-      s1 = fmaf(av.x, v1[4 * q], fmaf(av.y, v1[4 * q + 1],
-                fmaf(av.z, v1[4 * q + 2], fmaf(av.w, v1[4 * q + 3], s1))));
+    for (int c = 0; c < W; ++c) {
+      vout[at0 + c * N3] = g0[c] + u0[c];
+      vout[at1 + c * N3] = g1[c] + u1[c];
     }
-    if (last) {
-      vout[at0 + oc * N3] = s0;
-      vout[at1 + oc * N3] = s1;
-    } else {
-      zsave[at0 + oc * N3] = s0;
-      zsave[at1 + oc * N3] = s1;
-      vout[at0 + oc * N3] = gelu(s0);
-      vout[at1 + oc * N3] = gelu(s1);
+  } else {
+    float v0[W], v1[W];
+#pragma unroll
+    for (int c = 0; c < W; ++c) {
+      v0[c] = vin[at0 + c * N3];
+      v1[c] = vin[at1 + c * N3];
+    }
+#pragma unroll
+    for (int oc = 0; oc < W; ++oc) {
+      float s0 = Al[W * W + oc] + u0[oc], s1 = Al[W * W + oc] + u1[oc];
+      const float4* ar = reinterpret_cast<const float4*>(Al + oc * W);
+#pragma unroll
+      for (int q = 0; q < W / 4; ++q) {
+        const float4 av = ar[q];
+        s0 = fmaf(av.x, v0[4 * q], fmaf(av.y, v0[4 * q + 1],
+                  fmaf(av.z, v0[4 * q + 2], fmaf(av.w, v0[4 * q + 3], s0))));
+        s1 = fmaf(av.x, v1[4 * q], fmaf(av.y, v1[4 * q + 1],
+                  fmaf(av.z, v1[4 * q + 2], fmaf(av.w, v1[4 * q + 3], s1))));
+      }
+      if (last) {
+        vout[at0 + oc * N3] = s0;
+        vout[at1 + oc * N3] = s1;
+      } else {
+        zsave[at0 + oc * N3] = s0;
+        zsave[at1 + oc * N3] = s1;
+        vout[at0 + oc * N3] = gelu(s0);
+        vout[at1 + oc * N3] = gelu(s1);
+      }
     }
   }
 }
@@ -539,6 +552,74 @@ struct TileAcc {
   }
 };
 
+// Register-tiled variant for NA, NB multiples of 4: the tile is staged
+// voxel-major (row j = voxel, stride LDL / LDR = 4 mod 8 floats, so that the
+// 16-byte row writes of 8 consecutive threads hit distinct banks); a thread
+// owns a 4 x 4 block of entries and every S-th voxel of the tile (2 x 16-byte
+// loads per 16 FMA), and the S voxel slices are added in a fixed order at the
+// end.  Row sums come with the b = 0 blocks.
+template <int NA, int NB>
+struct TileAcc4 {
+  static_assert(NA % 4 == 0 && NB % 4 == 0, "4 x 4 entry blocks");
+  static constexpr int LDL = (NA % 8 == 4) ? NA : NA + 4;
+  static constexpr int LDR = (NB % 8 == 4) ? NB : NB + 4;
+  static constexpr int TB = NB / 4, NT = (NA / 4) * TB;
+  static constexpr int S = kThreads / NT;      // voxel slices
+  static constexpr int NE = NA * NB + NA;
+  static constexpr int SMEM = kThreads * (LDL + LDR);   // staging floats (>= S * NE)
+  static_assert(S * NE <= SMEM, "slice reduction fits the staging area");
+  float acc[4][4], rs[4];
+  int ai, bi, sl;
+  bool active;
+  __device__ void init() {
+    const int t = threadIdx.x;
+    active = t < NT * S;
+    const int tile = t % NT;
+    sl = t / NT;
+    ai = tile / TB;
+    bi = tile - ai * TB;
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      rs[x] = 0.f;
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
+    }
+  }
+  // all threads call this once per tile, after writing row threadIdx.x of sL / sR
+  __device__ void step(const float* sL, const float* sR) {
+    if (!active) return;
+    for (int j = sl; j < kThreads; j += S) {
+      const float4 l = *reinterpret_cast<const float4*>(sL + j * LDL + 4 * ai);
+      const float4 r = *reinterpret_cast<const float4*>(sR + j * LDR + 4 * bi);
+      const float lv[4] = {l.x, l.y, l.z, l.w}, rv[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        rs[x] += lv[x];
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(lv[x], rv[y], acc[x][y]);
+      }
+    }
+  }
+  // scratch: SMEM floats of shared memory no thread still reads (call after a barrier)
+  __device__ void store(float* part, float* scratch) const {
+    if (active) {
+      float* sc = scratch + sl * NE;
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+#pragma unroll
+        for (int y = 0; y < 4; ++y) sc[(4 * ai + x) * NB + 4 * bi + y] = acc[x][y];
+        if (bi == 0) sc[NA * NB + 4 * ai + x] = rs[x];
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < NE; e += kThreads) {
+      float v = 0.f;
+      for (int q = 0; q < S; ++q) v += scratch[q * NE + e];
+      part[e] = v;
+    }
+  }
+};
+
 // v0 = P f + p.   total = B N^3 voxels.
 __global__ void __launch_bounds__(kThreads) k_lift(const float* __restrict__ feat,
                                                    const float* __restrict__ prm,
@@ -610,9 +691,10 @@ __global__ void __launch_bounds__(kThreads) k_bwd_pw(const float* __restrict__ d
                                                      float* __restrict__ dvprev,
                                                      float* __restrict__ part, long long N3,
                                                      int B, int last) {
-  using Acc = TileAcc<W, W>;
-  __shared__ float sL[W * Acc::LD];
-  __shared__ float sR[W * Acc::LD];
+  using Acc = TileAcc4<W, W>;
+  __shared__ __align__(16) float stage[Acc::SMEM];
+  float* sL = stage;                     // [voxel][LDL]
+  float* sR = stage + kThreads * Acc::LDL;
   __shared__ float As[W * W];
   for (int i = threadIdx.x; i < W * W; i += kThreads) As[i] = layer[i];
   __syncthreads();
@@ -622,20 +704,20 @@ __global__ void __launch_bounds__(kThreads) k_bwd_pw(const float* __restrict__ d
   const int t = threadIdx.x;
   RPM_FNO_TILE_LOOP(total) {
     const long long gidx = base + t;
+    float d[W], x[W];
     if (gidx < total) {
       const int b = (int)(gidx / N3);
       const long long vox = gidx - b * N3;
-      float d[W];
 #pragma unroll
       for (int o = 0; o < W; ++o) {
         const long long at = ((long long)b * W + o) * N3 + vox;
         float g = dv[at];
         if (!last) g *= gelu_grad(zs[at]);
         d[o] = g;
-        dz[at] = g;
-        sL[o * Acc::LD + t] = g;
-        sR[o * Acc::LD + t] = v[at];
+        x[o] = v[at];
       }
+#pragma unroll
+      for (int o = 0; o < W; ++o) dz[((long long)b * W + o) * N3 + vox] = d[o];
 #pragma unroll
       for (int c = 0; c < W; ++c) {
         float s = 0.f;
@@ -645,22 +727,26 @@ __global__ void __launch_bounds__(kThreads) k_bwd_pw(const float* __restrict__ d
       }
     } else {
 #pragma unroll
-      for (int o = 0; o < W; ++o) {
-        sL[o * Acc::LD + t] = 0.f;
-        sR[o * Acc::LD + t] = 0.f;
-      }
+      for (int o = 0; o < W; ++o) d[o] = x[o] = 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < W / 4; ++q) {
+      *reinterpret_cast<float4*>(sL + t * Acc::LDL + 4 * q) =
+          make_float4(d[4 * q], d[4 * q + 1], d[4 * q + 2], d[4 * q + 3]);
+      *reinterpret_cast<float4*>(sR + t * Acc::LDR + 4 * q) =
+          make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
     }
     __syncthreads();
     acc.step(sL, sR);
     __syncthreads();
   }
-  acc.store(part + (long long)blockIdx.x * Acc::NE);
+  acc.store(part + (long long)blockIdx.x * Acc::NE, stage);
 }
 
 // Shared memory of k_head (floats): the two tiles, then per sample the
 // contracted maps QE_b[o][c] (c < W) and qE_b[o] (c = W), then E.
 size_t head_smem(int B) {
-  return ((size_t)(NH + W) * (kThreads + 1) + (size_t)B * COUT * (W + 1) + (size_t)B * CE) * 4;
+  return ((size_t)TileAcc4<NH, W>::SMEM + (size_t)B * COUT * (W + 1) + (size_t)B * CE) * 4;
 }
 
 // Localisation head: H = Q v + q (36 channels, channel 6 o + j = H[o][j]) and
@@ -676,11 +762,11 @@ __global__ void __launch_bounds__(kThreads) k_head(const float* __restrict__ v,
                                                    float* __restrict__ dv,
                                                    float* __restrict__ part, long long N3, int B,
                                                    float inv_nel) {
-  using Acc = TileAcc<NH, W>;
+  using Acc = TileAcc4<NH, W>;
   extern __shared__ float4 smem4[];
-  float* sL = (float*)smem4;                 // [NH][LD]
-  float* sR = sL + NH * Acc::LD;             // [W][LD]
-  float* QE = sR + W * Acc::LD;              // [B][COUT][W + 1]
+  float* sL = (float*)smem4;                 // [voxel][LDL]
+  float* sR = sL + kThreads * Acc::LDL;      // [voxel][LDR]
+  float* QE = (float*)smem4 + Acc::SMEM;     // [B][COUT][W + 1]
   float* Es = QE + B * COUT * (W + 1);       // [B][CE]
   __shared__ float red[kThreads / 32];
   for (int i = threadIdx.x; i < B * CE; i += kThreads) Es[i] = Ed[i];
@@ -731,20 +817,20 @@ __global__ void __launch_bounds__(kThreads) k_head(const float* __restrict__ v,
 #pragma unroll
           for (int o = 0; o < COUT; ++o) s = fmaf(qe[o * (W + 1) + c], d[o], s);
           dv[((long long)b * W + c) * N3 + vox] = s;
-          sR[c * Acc::LD + t] = x[c];
+          sR[t * Acc::LDR + c] = x[c];
         }
 #pragma unroll
         for (int o = 0; o < COUT; ++o)
 #pragma unroll
-          for (int j = 0; j < CE; ++j) sL[(o * CE + j) * Acc::LD + t] = d[o] * Es[b * CE + j];
+          for (int j = 0; j < CE; ++j) sL[t * Acc::LDL + o * CE + j] = d[o] * Es[b * CE + j];
       }
     }
     if (target) {
       if (!have) {
 #pragma unroll
-        for (int k = 0; k < NH; ++k) sL[k * Acc::LD + t] = 0.f;
+        for (int k = 0; k < NH; ++k) sL[t * Acc::LDL + k] = 0.f;
 #pragma unroll
-        for (int c = 0; c < W; ++c) sR[c * Acc::LD + t] = 0.f;
+        for (int c = 0; c < W; ++c) sR[t * Acc::LDR + c] = 0.f;
       }
       __syncthreads();
       acc.step(sL, sR);
@@ -752,7 +838,7 @@ __global__ void __launch_bounds__(kThreads) k_head(const float* __restrict__ v,
     }
   }
   if (!target) return;
-  acc.store(part + (long long)blockIdx.x * kNeHead);
+  acc.store(part + (long long)blockIdx.x * kNeHead, (float*)smem4);   // after the loop's barrier
   for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
   if ((t & 31) == 0) red[t >> 5] = sq;
   __syncthreads();
