@@ -7,9 +7,11 @@
 //               plane restricted to kx < m, then the y transform restricted to
 //               the 2m kept ky; writes the [ncol = 2m * m][W] mode columns of
 //               the plane.
-//   k_spec_fwd  block per kept (ky, kx) column, looping over the batch: z
-//               transform to the 2m kept kz, complex channel mixing with the
-//               column's R (held in shared memory), inverse z transform.
+//   k_spec_fwd  block per (kept (ky, kx) column, sample): z transform to the
+//               2m kept kz, complex channel mixing with the column's R (held
+//               in shared memory), inverse z transform.  The backward
+//               (k_spec_bwd) loops over the batch in one block per column so
+//               that the R gradient is summed without atomics.
 //   k_inv_xy    block per (y chunk, z, b): inverse y then inverse x transform
 //               of the 16 channels, fused with the pointwise branch
 //               A v + a and the activation (forward) or with the accumulation
@@ -210,7 +212,15 @@ __global__ void __launch_bounds__(kThreads) k_xy_fwd(const float* __restrict__ s
 
 size_t spec_smem(int N, int m) {
   const size_t m2 = 2 * m;
-  return (m2 * W * W + (size_t)N * W + 3 * m2 * W + N) * sizeof(float2);
+  return (m2 * W * W + (size_t)N * W + 3 * m2 * W + N + (size_t)N * m2) * sizeof(float2);
+}
+
+// Tz[z][kz_i] = exp(-2 pi i kz z / N) for the kept kz (the inverse uses the conjugate).
+__device__ __forceinline__ void z_table(const float2* twg, float2* Tz, int N, int m) {
+  for (int i = threadIdx.x; i < N * 2 * m; i += kThreads) {
+    const int z = i / (2 * m), k = i - z * (2 * m);
+    Tz[i] = twg[(kfreq(k, m, N) * z) % N];
+  }
 }
 
 // z transform of the column's [N][W] values to the 2m kept kz: out[kz_i][c].
@@ -233,14 +243,14 @@ __device__ __forceinline__ void z_dft(const float2* a, const float2* tw, float2*
 }
 
 // inverse z transform (no weights) of U[kz_i][c] to dst[z][c] (column stride given).
-__device__ __forceinline__ void z_idft(const float2* U, const float2* tw, float2* dst,
+__device__ __forceinline__ void z_idft(const float2* U, const float2* Tz, float2* dst,
                                        long long zstride, int N, int m) {
   for (int o = threadIdx.x; o < N * W; o += kThreads) {
     const int z = o / W, c = o % W;
     float re = 0.f, im = 0.f;
+    const float2* tz = Tz + z * 2 * m;
     for (int kzi = 0; kzi < 2 * m; ++kzi) {
-      const int kz = kfreq(kzi, m, N);
-      const float2 u = U[kzi * W + c], t = tw[(kz * z) % N];
+      const float2 u = U[kzi * W + c], t = tz[kzi];
       re += u.x * t.x + u.y * t.y;   // u * conj(t)
       im += u.y * t.x - u.x * t.y;
     }
@@ -261,33 +271,33 @@ __global__ void __launch_bounds__(kThreads) k_spec_fwd(const float2* __restrict_
   float2* a = Rs + m2 * W * W;      // [z][c]
   float2* V = a + N * W;            // [kz_i][c]
   float2* U = V + m2 * W;
-  float2* tw = U + m2 * W;
+  float2* tw = U + 2 * m2 * W;
+  float2* Tz = tw + N;
+  const int b = blockIdx.y;   // one sample per block
   const float4* r4 = (const float4*)(R + (long long)col * m2 * W * W);
   for (int i = tid; i < m2 * W * W / 2; i += kThreads) ((float4*)Rs)[i] = r4[i];
   for (int i = tid; i < N; i += kThreads) tw[i] = twg[i];
-  for (int b = 0; b < B; ++b) {
-    __syncthreads();
-    for (int i = tid; i < N * W; i += kThreads)
-      a[i] = A2[((long long)b * N + i / W) * ncol * W + col * W + i % W];
-    __syncthreads();
-    z_dft(a, tw, V, N, m, 1.f);
-    __syncthreads();
-    float2* vs = Vs + ((long long)col * B + b) * m2 * W;
-    for (int o = tid; o < m2 * W; o += kThreads) {
-      vs[o] = V[o];
-      const int kzi = o / W, oc = o % W;
-      float re = 0.f, im = 0.f;
+  z_table(twg, Tz, N, m);
+  for (int i = tid; i < N * W; i += kThreads)
+    a[i] = A2[((long long)b * N + i / W) * ncol * W + col * W + i % W];
+  __syncthreads();
+  z_dft(a, tw, V, N, m, 1.f);
+  __syncthreads();
+  float2* vs = Vs + ((long long)col * B + b) * m2 * W;
+  for (int o = tid; o < m2 * W; o += kThreads) {
+    vs[o] = V[o];
+    const int kzi = o / W, oc = o % W;
+    float re = 0.f, im = 0.f;
 #pragma unroll
-      for (int i = 0; i < W; ++i) {
-        const float2 v = V[kzi * W + i], r = Rs[(kzi * W + i) * W + oc];
-        re += v.x * r.x - v.y * r.y;
-        im += v.x * r.y + v.y * r.x;
-      }
-      U[o] = make_float2(re, im);
+    for (int i = 0; i < W; ++i) {
+      const float2 v = V[kzi * W + i], r = Rs[(kzi * W + i) * W + oc];
+      re += v.x * r.x - v.y * r.y;
+      im += v.x * r.y + v.y * r.x;
     }
-    __syncthreads();
-    z_idft(U, tw, Bz + (long long)b * N * ncol * W + col * W, (long long)ncol * W, N, m);
+    U[o] = make_float2(re, im);
   }
+  __syncthreads();
+  z_idft(U, Tz, Bz + (long long)b * N * ncol * W + col * W, (long long)ncol * W, N, m);
 }
 
 // Backward of k_spec_fwd.  A2 holds the xy transform of dz; dU = w(kx) / N^3 *
@@ -307,11 +317,13 @@ __global__ void __launch_bounds__(kThreads) k_spec_bwd(const float2* __restrict_
   float2* V = dU + m2 * W;
   float2* dV = V + m2 * W;
   float2* tw = dV + m2 * W;
+  float2* Tz = tw + N;
   const int kx = col % m;
   const float wgt = (kx == 0 ? 1.f : 2.f) * inv_n3;
   const float4* r4 = (const float4*)(R + (long long)col * m2 * W * W);
   for (int i = tid; i < m2 * W * W / 2; i += kThreads) ((float4*)Rs)[i] = r4[i];
   for (int i = tid; i < N; i += kThreads) tw[i] = twg[i];
+  z_table(twg, Tz, N, m);
   const int gi = tid / W, go = tid % W;   // this thread's (i, o) entry of gR
   float2 g[2 * kMaxModes];
 #pragma unroll
@@ -345,7 +357,7 @@ __global__ void __launch_bounds__(kThreads) k_spec_bwd(const float2* __restrict_
       dV[o] = make_float2(re, im);
     }
     __syncthreads();
-    z_idft(dV, tw, Bz + (long long)b * N * ncol * W + col * W, (long long)ncol * W, N, m);
+    z_idft(dV, Tz, Bz + (long long)b * N * ncol * W + col * W, (long long)ncol * W, N, m);
   }
   float2* gr = gR + (long long)col * m2 * W * W;
 #pragma unroll
@@ -990,7 +1002,7 @@ bool run_forward(rpm_fno* f, int B, const float* feat, const float* target, floa
   if (!fck(f, cudaGetLastError(), "lift")) return false;
   for (int l = 0; l < L; ++l) {
     k_xy_fwd<<<dim3(N, B), kThreads, xy_smem(N, m), f->st>>>(f->v(l), f->A2, f->tw, N, m);
-    k_spec_fwd<<<f->ncol, kThreads, spec_smem(N, m), f->st>>>(
+    k_spec_fwd<<<dim3(f->ncol, B), kThreads, spec_smem(N, m), f->st>>>(
         f->A2, (const float2*)(f->layer(l) + kLayerHead), f->Vsl(l), f->Bz, f->tw, N, m, B);
     const int last = (l == L - 1);
     k_inv_xy<false><<<dim3(N / f->YC, N, B), kThreads, inv_smem(m, f->YC), f->st>>>(
