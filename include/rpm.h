@@ -189,7 +189,8 @@ rpm_status rpm_apply_gamma(rpm_ctx* ctx, const float* in, const double E[6], flo
  *   phase    DEVICE pointer, uint8 [nz][ny][nx], ids < n_phases.
  *   phases   host array of n_phases (1..256) moduli; c0 the reference medium.
  *   in, out  device fields [6][n] (may not alias); E host double[6]
- *            (required for RPM_GAMMA_FULL_MAP); flags as rpm_apply_gamma.
+ *            (required for RPM_GAMMA_FULL_MAP); flags RPM_GAMMA_FULL_MAP,
+ *            RPM_GAMMA_LINEAR or RPM_GAMMA_RAW_TAU (RPM_GAMMA_PROJECT needs a context).
  *   cuda_stream  stream for the copies and kernels (NULL: legacy stream).
  * The first call on a device looks up the arrays' device addresses; make that
  * first call before any stream capture.  Each call copies its tables into
@@ -212,6 +213,12 @@ rpm_status rpm_apply_gamma_noalloc(const rpm_grid* grid, const uint8_t* phase, i
  *   eps_out    optional output strain field; sig_out optional stress field.
  *   out_on_host  0: eps_out/sig_out are device pointers; 1: host pointers.
  *   info       optional; filled also on failure.
+ * Float32 fields need two measures the paper's double-precision setting does
+ * not: no basis growth from iterate differences below 1e-5 |xi| (the
+ * rounding level of F), and, when the residual has not halved in
+ * 3 (n_max + 1) steps, re-centring: the iterate is split as eps = base + y
+ * and the iteration continues on y with the same linear part and the defect
+ * F(base) - base (same fixed point; at most 16 times per solve).
  * Synchronises the context stream before returning.
  */
 rpm_status rpm_solve(rpm_ctx* ctx, const double E[6], const float* eps0, float* eps_out,
