@@ -83,11 +83,10 @@ __device__ __forceinline__ float dot4(float4 a, float4 b) {
 // many digits (near convergence).
 // Partial sums go to rows [0] (the norm) and [1 + row0 + j] of `partials`.
 template <int KMAX>
-__global__ void __launch_bounds__(kRedThreads) k_dots(const float4* __restrict__ x,
-                                                      const float4* __restrict__ xm,
-                                                      const float4* __restrict__ Y, long long ys4,
-                                                      int K, int row0, long long n4,
-                                                      double* partials, int nblk) {
+__device__ __forceinline__ void dots_body(const float4* __restrict__ x,
+                                          const float4* __restrict__ xm,
+                                          const float4* __restrict__ Y, long long ys4, int K,
+                                          int row0, long long n4, double* partials, int nblk) {
   float acc[KMAX + 1];
 #pragma unroll
   for (int j = 0; j <= KMAX; ++j) acc[j] = 0.f;
@@ -111,6 +110,81 @@ __global__ void __launch_bounds__(kRedThreads) k_dots(const float4* __restrict__
     }
   }
   block_store<KMAX + 1>(acc, K + 1, row0, partials, nblk);
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(kRedThreads) k_dots(const float4* __restrict__ x,
+                                                      const float4* __restrict__ xm,
+                                                      const float4* __restrict__ Y, long long ys4,
+                                                      int K, int row0, long long n4,
+                                                      double* partials, int nblk) {
+  dots_body<KMAX>(x, xm, Y, ys4, K, row0, n4, partials, nblk);
+}
+
+// k_dots (K <= 32) whose last block to finish also adds the per-block rows in
+// a fixed order (a warp per row: lanes take every 32nd block, then a fixed
+// shuffle tree) into sums[0..K] and, when M is given, takes the Newton step
+// of k_newton with p = K.  The ticket counter is zero between launches (the
+// last block resets it).  One launch instead of three.
+template <int KMAX>
+__global__ void __launch_bounds__(kRedThreads) k_dots_fused(
+    const float4* __restrict__ x, const float4* __restrict__ xm, const float4* __restrict__ Y,
+    long long ys4, int K, long long n4, double* partials, int nblk, double* sums,
+    unsigned int* ticket, const double* __restrict__ M, double* c, double* res_out,
+    double inv_norm) {
+  dots_body<KMAX>(x, xm, Y, ys4, K, 0, n4, partials, nblk);
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int j = warp; j <= K; j += kRedThreads / 32) {
+    double v = 0.0;
+    for (int b = lane; b < nblk; b += 32) v += __ldcg(partials + (size_t)j * nblk + b);   // L2
+    v = warp_sum(v);
+    if (lane == 0) sums[j] = v;
+  }
+  __syncthreads();
+  if (M) {
+    __shared__ double d[32];
+    for (int j = threadIdx.x; j < K; j += blockDim.x) d[j] = sums[1 + j];
+    __syncthreads();
+    for (int j = threadIdx.x; j < K; j += blockDim.x) {
+      double t = -d[j];
+      for (int k = 0; k < K; ++k) t += M[(size_t)j * K + k] * d[k];
+      c[j] = t;
+    }
+    if (threadIdx.x == 0) res_out[0] = sqrt(sums[0]) * inv_norm;   // NaN stays NaN
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+}
+
+cudaError_t launch_dots_fused(const float* x, const float* x_minus, const float* Y,
+                              long long ystride, int K, long long n, double* partials, int nblk,
+                              double* sums, unsigned int* ticket, const double* M, double* c,
+                              double* res_out, double inv_norm, cudaStream_t st) {
+  if (K > 32) return cudaErrorInvalidValue;
+  const long long n4 = n / 4;
+  const float4* x4 = reinterpret_cast<const float4*>(x);
+  const float4* m4 = reinterpret_cast<const float4*>(x_minus);
+  const float4* y4 = reinterpret_cast<const float4*>(Y);
+  const long long ys4 = ystride / 4;
+#define RPM_FUSED(KM)                                                                       \
+  k_dots_fused<KM><<<nblk, kRedThreads, 0, st>>>(x4, m4, y4, ys4, K, n4, partials, nblk, sums, \
+                                                 ticket, M, c, res_out, inv_norm)
+  if (K <= 2)
+    RPM_FUSED(2);
+  else if (K <= 8)
+    RPM_FUSED(8);
+  else if (K <= 16)
+    RPM_FUSED(16);
+  else
+    RPM_FUSED(32);
+#undef RPM_FUSED
+  return cudaGetLastError();
 }
 
 int dots_blocks_for(long long n) {

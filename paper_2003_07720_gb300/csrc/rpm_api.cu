@@ -40,6 +40,7 @@ constexpr int kMaxRebase = 16;        // re-centrings of one solve (see solve_im
 constexpr double kGrowNoise = 1e-5;
 constexpr int kM = kRes + 8;          // (I - H)^-1, kPCap x kPCap
 constexpr int kSmall = kM + kPCap * kPCap;
+constexpr int kTicket = kSmall;       // one more slot: the fused reduction's counter
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -253,13 +254,27 @@ struct Ops {
     return ok;
   }
   // sums[0..K] <- dots of x against Y (see launch_dots)
-  bool dots(const float* x, const float* xm, const float* Y, int K, double* sums) {
+  // sums[0..K] <- dots (see launch_dots); with M, also the Newton step into c
+  // and the residual (K <= 32: one fused launch)
+  bool dots(const float* x, const float* xm, const float* Y, int K, double* sums,
+            const double* M = nullptr, double* cN = nullptr, double* res = nullptr,
+            double inv_norm = 0.0) {
     const size_t m = mark(1);
-    c->launches += 1 + dots_launches(K);
     c->proj_bytes += (double)(K + 1 + (xm ? 1 : 0)) * (double)c->fsz * 4.0;
-    bool ok = ck(c, launch_dots(x, xm, Y, (long long)c->fst, K, c->n, c->partials, c->nblk, c->st),
-                 "dots") &&
-              ck(c, launch_reduce_partials(c->partials, c->nblk, K + 1, sums, c->st), "reduce");
+    bool ok;
+    if (K <= 32) {
+      c->launches += 1;
+      ok = ck(c, launch_dots_fused(x, xm, Y, (long long)c->fst, K, c->n, c->partials, c->nblk,
+                                   sums, reinterpret_cast<unsigned int*>(c->dsmall + kTicket), M,
+                                   cN, res, inv_norm, c->st),
+              "dots");
+    } else {
+      c->launches += 1 + dots_launches(K) + (M ? 1 : 0);
+      ok = ck(c, launch_dots(x, xm, Y, (long long)c->fst, K, c->n, c->partials, c->nblk, c->st),
+              "dots") &&
+           ck(c, launch_reduce_partials(c->partials, c->nblk, K + 1, sums, c->st), "reduce") &&
+           (!M || ck(c, launch_newton(sums, K, M, cN, res, inv_norm, c->st), "newton"));
+    }
     done(m);
     return ok;
   }
@@ -469,7 +484,7 @@ rpm_status rpm_create(const rpm_grid* grid, const uint8_t* phase, int phase_on_d
   const size_t spec_bytes = (size_t)6 * nz * g.plane * sizeof(float2);
   const size_t need = tab_bytes + align_up((size_t)c->n, 256) + spec_bytes + kFields * fbytes +
                       2 * (size_t)c->p_cap * fbytes + (size_t)(kPCap + 1) * c->nblk * 8 +
-                      kSmall * 8;
+                      (kSmall + 1) * 8;
   if (o.max_device_gb > 0 && (double)need > o.max_device_gb * 1e9) {
     rpm_destroy(c);
     return RPM_ERR_OOM;
@@ -488,7 +503,7 @@ rpm_status rpm_create(const rpm_grid* grid, const uint8_t* phase, int phase_on_d
       (e = alloc((void**)&c->Z, (size_t)c->p_cap * fbytes)) != cudaSuccess ||
       (e = alloc((void**)&c->W, (size_t)c->p_cap * fbytes)) != cudaSuccess ||
       (e = alloc((void**)&c->partials, (size_t)(kPCap + 1) * c->nblk * 8)) != cudaSuccess ||
-      (e = alloc((void**)&c->dsmall, kSmall * 8)) != cudaSuccess) {
+      (e = alloc((void**)&c->dsmall, (kSmall + 1) * 8)) != cudaSuccess) {
     cudaGetLastError();
     rpm_destroy(c);
     return e == cudaErrorMemoryAllocation ? RPM_ERR_OOM : RPM_ERR_CUDA;
@@ -515,7 +530,7 @@ rpm_status rpm_create(const rpm_grid* grid, const uint8_t* phase, int phase_on_d
       put(o_fy, fy.data(), fy.size() * 8) != cudaSuccess ||
       put(o_dm, dm256.data(), 256 * 8) != cudaSuccess ||
       put(o_cm, cm256.data(), 256 * 8) != cudaSuccess ||
-      cudaMemsetAsync(c->dsmall, 0, kSmall * 8, c->st) != cudaSuccess ||
+      cudaMemsetAsync(c->dsmall, 0, (kSmall + 1) * 8, c->st) != cudaSuccess ||
       cudaStreamSynchronize(c->st) != cudaSuccess) {
     rpm_destroy(c);
     return RPM_ERR_CUDA;
@@ -606,7 +621,7 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
   std::vector<double> M;
 
   if (!ck(c, cudaEventRecord(c->ev0, c->st), "event")) return RPM_ERR_CUDA;
-  if (!ck(c, cudaMemsetAsync(ds, 0, kSmall * 8, c->st), "memset")) return RPM_ERR_CUDA;
+  if (!ck(c, cudaMemsetAsync(ds, 0, (kSmall + 1) * 8, c->st), "memset")) return RPM_ERR_CUDA;
   float* eps_cur = epsb[0];
   if (eps0) {
     if (!ck(c, cudaMemcpyAsync(eps_cur, eps0, c->fsz * 4, cudaMemcpyDeviceToDevice, c->st), "eps0"))
@@ -636,12 +651,13 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
   };
 
   // residual, zeta - z = Z^T (xi - eps) and the Newton correction for the current pair (eps, xi)
-  auto eval = [&](double& r) -> bool {
-    if (!ops.dots(xi[cur], eps_cur, c->Z, c->p, ds + kSums)) return false;
-    c->launches += 1;
-    if (!ck(c, launch_newton(ds + kSums, c->p, ds + kM, ds + kC, ds + kRes, inv_norm, c->st),
-            "newton"))
+  // (read = false: leave the residual on the device; the Newton correction is
+  // all the next step needs)
+  auto eval = [&](double& r, bool read = true) -> bool {
+    if (!ops.dots(xi[cur], eps_cur, c->Z, c->p, ds + kSums, ds + kM, ds + kC, ds + kRes,
+                  inv_norm))
       return false;
+    if (!read) return true;
     if (!ops.read_small(kRes, 1)) return false;
     r = hs[kRes];
     return true;
@@ -780,8 +796,12 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
     // Without a basis the steps need no host decision between them: run up to
     // kBatch of them back to back and test the residual of the last one only
     // (never past a basis-growth point or max_iters).
+    // Steps between host reads of the residual: up to kBatch while the basis
+    // is empty, and with a basis while the residual is still far (> 100 tol)
+    // from the test and no residual history is recorded, never past a
+    // basis-growth point or max_iters.
     int batch = 1;
-    if (c->p == 0) {
+    if (c->p == 0 || (r > 1e2 * o.tol && !c->trace_res)) {
       batch = kBatch;
       if (c->p < std::min(o.p_max, c->p_cap)) batch = std::min(batch, o.n_max + 1 - nu);
       batch = std::max(1, std::min(batch, o.max_iters - it));
@@ -803,8 +823,14 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
       hist = std::min(hist + 1, 3);
       eps_cur = eps_next;
       // with an empty basis the residual is only needed where it is tested:
-      // after the last step of the batch (a non-finite value propagates to it)
-      if (b == batch - 1 && !eval(r)) return RPM_ERR_CUDA;
+      // after the last step of the batch (a non-finite value propagates to
+      // it); with a basis every step needs the Newton correction, but only
+      // the last one's residual is read
+      if (c->p == 0) {
+        if (b == batch - 1 && !eval(r)) return RPM_ERR_CUDA;
+      } else if (!eval(r, b == batch - 1)) {
+        return RPM_ERR_CUDA;
+      }
     }
     trace(it, r);
     // stall: no halving of the residual in 3 (n_max + 1) steps -> re-centre

@@ -58,6 +58,12 @@ cudaError_t launch_dots(const float* x, const float* x_minus /*nullable*/, const
                         cudaStream_t st);
 cudaError_t launch_reduce_partials(const double* partials, int nblk, int m, double* out,
                                    cudaStream_t st);
+// launch_dots + launch_reduce_partials (+ launch_newton when M is given, p = K)
+// in one launch, for K <= 32; ticket: a device counter that is zero on entry.
+cudaError_t launch_dots_fused(const float* x, const float* x_minus, const float* Y,
+                              long long ystride, int K, long long n, double* partials, int nblk,
+                              double* sums, unsigned int* ticket, const double* M, double* c,
+                              double* res_out, double inv_norm, cudaStream_t st);
 cudaError_t launch_combine(float* out, const float* x, float xscale, const float* Y,
                            long long ystride, int K, const double* coef, float cscale,
                            long long n, cudaStream_t st);
