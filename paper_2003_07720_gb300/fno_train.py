@@ -144,6 +144,7 @@ def evaluate(net: "fno.Fno", n: int, seeds, options=None):
                 row[name] = {"converged": info["converged"], "F": info["gamma_applies"],
                              "iters": info["iters"], "warm_iters": info["warm_iters"],
                              "ms": info["ms"], "guess_ms": round(t_net * 1e3, 3),
-                             "residual": info["residual"]}
+                             "residual": info["residual"],
+                             "mean_stress": list(info["mean_stress"])}
         rows.append(row)
     return rows

@@ -217,3 +217,37 @@ def test_warm_stage_from_uniform_eps0_equals_default_warm_form():
     assert (a["warm_iters"], a["iters"], a["gamma_applies"]) == (b["warm_iters"], b["iters"],
                                                                  b["gamma_applies"])
     assert a["mean_stress"] == b["mean_stress"]
+
+
+def test_trained_network_gain_is_measured(fno):
+    """Train the network on solver solutions (48 cells at 32^3, as the
+    64^3 study does at a smaller size), then solve held-out cells from the
+    cold start and from the learned guess.  Where both converge they reach
+    the same answer; the gain (cold minus learned F applications) and the
+    learned starts that fail are reported, not asserted: the 64^3 study finds
+    the gain near zero or negative, and on soft-inclusion cells Algorithm 2 on
+    Eq. 3.9 can diverge from a perturbed start where the start from E
+    converges (cell_fno_member(5004) at 32^3 diverges after 182 steps in the
+    FP64 oracle as on the GPU)."""
+    from paper_2003_07720_gb300 import fno_train
+    N, m, L, B = 32, 12, 4, 8
+    data = fno_train.make_dataset(N, list(range(1000, 1048)))
+    assert len(data.seeds) >= 24
+    with fno.Fno(N, m, L, max_batch=B) as net:
+        net.set_params(ms.fno_params(m, L, seed=0))
+        hist = fno_train.train(net, data, epochs=30, batch=B, lr=4e-3)
+        assert hist[-1] < 0.9 * hist[0], hist
+        rows = fno_train.evaluate(net, N, list(range(5000, 5006)))
+    gains, failed = [], []
+    for r in rows:
+        if not r["cold"]["converged"]:
+            continue
+        if not r["learned"]["converged"]:
+            failed.append(r["seed"])
+            continue
+        a, b = np.array(r["cold"]["mean_stress"]), np.array(r["learned"]["mean_stress"])
+        assert np.max(np.abs(a - b)) < 1e-4 * np.max(np.abs(a)), r
+        gains.append(r["cold"]["F"] - r["learned"]["F"])
+    assert gains, rows
+    print("F saved by the learned start per held-out cell:", gains,
+          "; learned starts that did not converge (cold did):", failed)
