@@ -142,10 +142,20 @@ __global__ void __launch_bounds__(kRedThreads) k_dots_fused(
   __threadfence();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int j = warp; j <= K; j += kRedThreads / 32) {
-    double v = 0.0;
-    for (int b = lane; b < nblk; b += 32) v += __ldcg(partials + (size_t)j * nblk + b);   // L2
-    v = warp_sum(v);
-    if (lane == 0) sums[j] = v;
+    // 8 independent chains per lane (loads in flight), added in a fixed order
+    const double* row = partials + (size_t)j * nblk;
+    double v[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    int b = lane;
+    for (; b + 7 * 32 < nblk; b += 8 * 32) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] += __ldcg(row + b + q * 32);   // L2, not L1
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (b + q * 32 < nblk) v[q] += __ldcg(row + b + q * 32);
+    double t = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+    t = warp_sum(t);
+    if (lane == 0) sums[j] = t;
   }
   __syncthreads();
   if (M) {

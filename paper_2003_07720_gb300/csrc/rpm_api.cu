@@ -41,6 +41,7 @@ constexpr double kGrowNoise = 1e-5;
 constexpr int kM = kRes + 8;          // (I - H)^-1, kPCap x kPCap
 constexpr int kSmall = kM + kPCap * kPCap;
 constexpr int kTicket = kSmall;       // one more slot: the fused reduction's counter
+constexpr int kFusedMaxBlocks = 1024; // dots blocks up to which the fused reduction pays
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -255,14 +256,15 @@ struct Ops {
   }
   // sums[0..K] <- dots of x against Y (see launch_dots)
   // sums[0..K] <- dots (see launch_dots); with M, also the Newton step into c
-  // and the residual (K <= 32: one fused launch)
+  // and the residual.  K <= 32 on grids up to ~100^3: one fused launch (the
+  // last block's serial tail costs more than two launches beyond that)
   bool dots(const float* x, const float* xm, const float* Y, int K, double* sums,
             const double* M = nullptr, double* cN = nullptr, double* res = nullptr,
             double inv_norm = 0.0) {
     const size_t m = mark(1);
     c->proj_bytes += (double)(K + 1 + (xm ? 1 : 0)) * (double)c->fsz * 4.0;
     bool ok;
-    if (K <= 32) {
+    if (K <= 32 && c->nblk <= kFusedMaxBlocks) {
       c->launches += 1;
       ok = ck(c, launch_dots_fused(x, xm, Y, (long long)c->fst, K, c->n, c->partials, c->nblk,
                                    sums, reinterpret_cast<unsigned int*>(c->dsmall + kTicket), M,
