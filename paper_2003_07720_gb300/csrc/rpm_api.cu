@@ -666,6 +666,7 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
   };
 
   // In(q, Z) of Algorithm 2 with the QR rule of Eq. 3.8.
+  bool want_rebase = false;
   auto grow = [&]() -> bool {
     const int prev = (cur + 2) % 3, prev2 = (cur + 1) % 3;
     double* one = ds + kSums;   // scratch sums
@@ -689,7 +690,10 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
     if (!(T11 > 0) || !std::isfinite(T11)) return true;
     if (!ops.dots(xi[cur], nullptr, nullptr, 0, ds + kSums)) return false;
     if (!ops.read_small(kSums, 1)) return false;
-    if (T11 < kGrowNoise * std::sqrt(std::max(hs[kSums], 0.0))) return true;   // rounding noise
+    if (T11 < kGrowNoise * std::sqrt(std::max(hs[kSums], 0.0))) {   // rounding noise:
+      want_rebase = true;   // re-centre, then grow from differences in the new coordinates
+      return true;
+    }
     const double T12 = d10 / T11;
     (void)n11;
     if (!ck(c, (++c->launches, launch_axpby)(D[1], 1.f, D[1], (float)(-T12 / T11), D[0], c->n, c->st), "axpby"))
@@ -774,6 +778,7 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
       return false;
     based = true;
     ++rebases;
+    hist = 1;   // growth waits for differences of iterates in the new coordinates
     return true;
   };
 
@@ -848,8 +853,14 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
     if (std::isfinite(r) && r > o.tol && r <= o.diverge_factor * r0 && nu > o.n_max) {
       if (c->p < std::min(o.p_max, c->p_cap) && hist == 3) {
         const int p_before = c->p;
+        want_rebase = false;
         if (!grow()) return RPM_ERR_CUDA;
         if (c->p != p_before && !eval(r)) return RPM_ERR_CUDA;
+        if (want_rebase && rebases < kMaxRebase) {
+          if (!rebase() || !eval(r)) return RPM_ERR_CUDA;
+          r_best = r;
+          it_best = it;
+        }
       }
       nu = 0;
     }
