@@ -215,10 +215,11 @@ rpm_status rpm_apply_gamma_noalloc(const rpm_grid* grid, const uint8_t* phase, i
  *   info       optional; filled also on failure.
  * Float32 fields need two measures the paper's double-precision setting does
  * not: no basis growth from iterate differences below 1e-5 |xi| (the
- * rounding level of F), and, when the residual has not halved in
- * 3 (n_max + 1) steps, re-centring: the iterate is split as eps = base + y
- * and the iteration continues on y with the same linear part and the defect
- * F(base) - base (same fixed point; at most 16 times per solve).
+ * rounding level of F), and re-centring, when such a growth is skipped or
+ * the residual has not halved in 3 (n_max + 1) steps: the iterate is split
+ * as eps = base + y and the iteration continues on y with the same linear
+ * part and the defect F(base) - base (same fixed point; at most 16 times per
+ * solve).
  * Synchronises the context stream before returning.
  */
 rpm_status rpm_solve(rpm_ctx* ctx, const double E[6], const float* eps0, float* eps_out,
