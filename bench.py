@@ -201,6 +201,21 @@ def oracle_reference_iters(form: str = "warm") -> int | None:
     return None
 
 
+def oracle_error(form: str, mean_stress) -> dict | None:
+    """Relative error of the GPU's mean stress against the FP64 oracle's own
+    converged solve of the same form (stored under tests/golden)."""
+    name = ("softincl128_warm_oracle_solve.json" if form == "warm"
+            else "nearvoid128_oracle_solve.json")
+    p = os.path.join(ROOT, "tests", "golden", name)
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        ref = np.array(json.load(f)["mean_stress"], float)
+    got = np.array(mean_stress, float)
+    return {"mean_stress_max_rel": float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))),
+            "reference": f"tests/golden/{name}"}
+
+
 def run_reference(args):
     world, rank, _ = dist_info()
     if rank != 0:
@@ -314,6 +329,8 @@ def run_ours(args):
                   "achieved": round(ach_gamma, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
                   "frac": round(ach_gamma / pk["hbm_gbs"], 4),
                   "traffic": recorded_traffic("gamma_apply_128"),
+                  "dram_gbs_from_traffic": (round(recorded_traffic("gamma_apply_128") / t_gamma / 1e9, 1)
+                                            if recorded_traffic("gamma_apply_128") else None),
                   "algorithmic_bytes_per_launch": alg_gamma,
                   "avg_launch_ms": round(t_gamma * 1e3, 4)}
     proj_line = {"bound": "hbm", "kernel": "projections (k_dots + k_reduce + k_combine)",
@@ -340,6 +357,19 @@ def run_ours(args):
                 "ms_per_step": round(c_ms / c_steps, 3), "iters": c_inf[0]["iters"],
                 "basis_size": c_inf[0]["basis_size"],
                 "mean_stress_11": c_inf[0]["mean_stress"][0]}
+
+    # the same form with the RPM stage's reference medium at 2x the matrix
+    c0x2 = None
+    if args.form == "warm" and not args.no_cold and world == 1:
+        cell2 = ms.cell_nearvoid(N, rank_seed(rank), c0_scale=2.0, e_incl=E_INCL)
+        ctx_2 = rpm.Context(cell2, opts, stream=stream)
+        c2_steps = max(1, min(args.steps, 5))
+        c2_ms, c2_inf = time_solves(ctx_2, E, c2_steps, 1, stream, flush, eps_out, raise_ok)
+        ctx_2.close()
+        c0x2 = {"value": round(c2_steps / (c2_ms / 1e3), 4), "unit": UNIT, "steps": c2_steps,
+                "iters": c2_inf[0]["iters"], "warm_iters": c2_inf[0]["warm_iters"],
+                "gamma_applies": c2_inf[0]["gamma_applies"],
+                "mean_stress_11": c2_inf[0]["mean_stress"][0]}
 
     # end to end through the C ABI with host buffers: phase map in, strain field out
     phase_host = np.ascontiguousarray(cell.phase)
@@ -382,6 +412,8 @@ def run_ours(args):
                     "residual": [i["residual"] for i in infos][:3],
                     "mean_stress_11": infos[0]["mean_stress"][0],
                     "cold_start": cold,
+                    "c0_2x_matrix": c0x2,
+                    "oracle_rel_err": oracle_error(args.form, infos[0]["mean_stress"]),
                     "parallelism": f"replicas x{world}"}),
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": round(e2e_value, 3), "unit": UNIT,
