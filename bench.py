@@ -539,8 +539,10 @@ def run_study_batch(args):
         C_seq.append(C)
     t_seq = time.perf_counter() - t0
     out["cell_by_cell_cold"] = {"seconds": round(t_seq, 3), "solves_per_s": round(n_solves / t_seq, 2)}
+    warm_tuned = rpm.rpm_default_options(tol=TOL, p_max=P_MAX, warm_tol=WARM_TOL, autotune=1)
     for name, opts, workers in (("batch_cold_1", cold, 1), ("batch_cold_w", cold, args.batch_workers),
-                                ("batch_warm_w", warm, args.batch_workers)):
+                                ("batch_warm_w", warm, args.batch_workers),
+                                ("batch_warm_w_autotuned", warm_tuned, args.batch_workers)):
         t0 = time.perf_counter()
         Cb, infos, stat, st = rpm.rpm_effective_stiffness_batch(cells, opts, n_workers=workers,
                                                                 raise_on_failure=False)

@@ -89,6 +89,9 @@ typedef struct {
   int warm_p_max;        /* RPM basis of the warm-start stage (default 0: plain Algorithm 3) */
   int warm_from_eps0;    /* 0 (default): a caller eps0 replaces the warm-start stage;
                             1: the stage runs from eps0 (e.g. a learned guess) */
+  int autotune;          /* 1: rpm_create times the z-pass tile variants (half, default
+                            and twice the pencils per block) on the context's grid and
+                            keeps the fastest; 0 (default): the default tile */
 } rpm_options;
 
 /* Fixed-point map wrapped by the solver.  BASIC: Eq. 3.9 (Algorithm 1).
@@ -269,6 +272,10 @@ const char* rpm_last_error(const rpm_ctx* ctx);
 
 /* Name of a status code. */
 const char* rpm_status_string(rpm_status s);
+
+/* Pencils per block of the z pass in use (the autotuner's choice when
+ * options.autotune was set at creation); 0 for a null context. */
+int rpm_pencil_tile(const rpm_ctx* ctx);
 
 /* Device bytes held by the context. */
 size_t rpm_device_bytes(const rpm_ctx* ctx);

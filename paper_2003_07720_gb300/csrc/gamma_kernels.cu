@@ -207,9 +207,12 @@ struct GammaArgs {
   float inv_mu0;
 };
 
-template <int NZ>
+// T consecutive (ky, kx) pencils per pass-B block: TT = 0 takes the default
+// for the length (8 pencils = 64-byte rows at nz >= 128); the tile autotuner
+// of rpm_create also tries half and twice the default (GridDev::pencil_t).
+template <int NZ, int TT = 0>
 struct PencilCfg {
-  static constexpr int T = NZ >= 128 ? 8 : (NZ >= 64 ? 16 : 32);   // 8 pencils: 64-byte rows
+  static constexpr int T = TT ? TT : (NZ >= 128 ? 8 : (NZ >= 64 ? 16 : 32));
   static constexpr int NZP = (NZ % 2 == 0) ? NZ + 1 : NZ;
 };
 
@@ -240,10 +243,10 @@ __device__ __forceinline__ void green_apply(float2* t, float n1, float n2, float
   t[5] = make_float2(-0.5f * (n1 * w2.x + n2 * w1.x), -0.5f * (n1 * w2.y + n2 * w1.y));
 }
 
-template <int NZ>
+template <int NZ, int TT>
 __global__ void __launch_bounds__(kThreads) k_pass_b(GridDev g, float2* __restrict__ spec, int mode,
                                                      GammaArgs ga) {
-  using C = PencilCfg<NZ>;
+  using C = PencilCfg<NZ, TT>;
   constexpr int T = C::T, NZP = C::NZP;
   extern __shared__ float2 sm[];
   float2* B = sm;
@@ -497,17 +500,30 @@ static cudaError_t launch_plane_passes(const GridDev& g, const float* in, float*
   return cudaGetLastError();
 }
 
+template <int NZ, int TT>
+static cudaError_t launch_pencil_tile(const GridDev& g, float2* spec, int mode,
+                                      const GammaArgs& ga, cudaStream_t st) {
+  using C = PencilCfg<NZ, TT>;
+  const size_t smem = (size_t)(6 * C::T * C::NZP + NZ) * sizeof(float2);
+  if (TT < 1 || smem > 227 * 1024) return cudaErrorInvalidValue;   // variant not available
+  cudaError_t e = set_smem(k_pass_b<NZ, TT>, smem);
+  if (e != cudaSuccess) return e;
+  const int blocks = (g.plane + C::T - 1) / C::T;
+  k_pass_b<NZ, TT><<<blocks, kThreads, smem, st>>>(g, spec, mode, ga);
+  return cudaGetLastError();
+}
+
 template <int NZ>
 static cudaError_t launch_pencil_pass(const GridDev& g, float2* spec, int mode, const GammaArgs& ga,
                                       cudaStream_t st) {
-  using C = PencilCfg<NZ>;
-  const size_t smem = (size_t)(6 * C::T * C::NZP + NZ) * sizeof(float2);
-  cudaError_t e = set_smem(k_pass_b<NZ>, smem);
-  if (e != cudaSuccess) return e;
-  const int blocks = (g.plane + C::T - 1) / C::T;
-  k_pass_b<NZ><<<blocks, kThreads, smem, st>>>(g, spec, mode, ga);
-  return cudaGetLastError();
+  constexpr int T0 = PencilCfg<NZ>::T;
+  switch (g.pencil_t) {
+    case 1: return launch_pencil_tile<NZ, (T0 / 2 > 0 ? T0 / 2 : 1)>(g, spec, mode, ga, st);
+    case 2: return launch_pencil_tile<NZ, 2 * T0>(g, spec, mode, ga, st);
+    default: return launch_pencil_tile<NZ, T0>(g, spec, mode, ga, st);
+  }
 }
+
 
 template <int NX>
 static cudaError_t launch_rows(const GridDev& g, const float* in, float* out, float2* spec,
@@ -617,6 +633,19 @@ static cudaError_t dispatch_pencil(const GridDev& g, float2* spec, int mode, con
 }
 
 int gamma_launches(int nx, int ny) { return plane_fits(nx, ny) ? 3 : 5; }
+
+int pencil_tile(const GridDev& g) {
+  int t0;
+  switch (g.nz) {
+#define RPM_CASE(N) \
+  case N: t0 = PencilCfg<N>::T; break;
+    RPM_Z_SIZES(RPM_CASE)
+#undef RPM_CASE
+    default: return 0;
+  }
+  return g.pencil_t == 1 ? (t0 / 2 > 0 ? t0 / 2 : 1) : (g.pencil_t == 2 ? 2 * t0 : t0);
+}
+
 
 bool grid_supported(int nx, int ny, int nz) {
   return xy_size_ok(nx) && xy_size_ok(ny) && z_size_ok(nz);

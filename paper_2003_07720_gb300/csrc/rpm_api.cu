@@ -118,7 +118,8 @@ bool valid_options(const rpm_options& o) {
          (o.scheme == RPM_SCHEME_BASIC || o.scheme == RPM_SCHEME_POLARIZATION) &&
          std::isfinite(o.alpha) && std::isfinite(o.beta) && std::isfinite(o.warm_tol) &&
          o.warm_c0_scale > 0 && o.warm_max_iters >= 0 && o.warm_p_max >= 0 &&
-         o.warm_p_max <= kPCap && (o.warm_from_eps0 == 0 || o.warm_from_eps0 == 1);
+         o.warm_p_max <= kPCap && (o.warm_from_eps0 == 0 || o.warm_from_eps0 == 1) &&
+         (o.autotune == 0 || o.autotune == 1);
 }
 
 // Per-phase (lam - lam0, mu - mu0) for the polarization of pass A.
@@ -132,6 +133,43 @@ cudaError_t upload_dmat(rpm_ctx* c) {
 }
 
 cudaError_t upload_scheme_tables(rpm_ctx* c);
+
+// Tile autotuner: time one Gamma0 application (linear part, zeroed fields)
+// with each z-pass tile variant on this context's grid, keep the fastest.
+bool autotune_tiles(rpm_ctx* c) {
+  float* in = c->fields;
+  float* out = c->fields + c->fst;
+  if (!ck(c, cudaMemsetAsync(in, 0, c->fsz * 4, c->st), "autotune") ||
+      !ck(c, cudaMemsetAsync(c->spec, 0, (size_t)6 * c->g.nz * c->g.plane * sizeof(float2), c->st),
+          "autotune"))
+    return false;
+  float best = 1e30f;
+  int best_v = 0;
+  for (int v = 0; v < 3; ++v) {
+    GridDev g = c->g;
+    g.pencil_t = v;
+    if (launch_apply_gamma(g, in, out, c->spec, nullptr, GM_LINEAR, c->st) != cudaSuccess) {
+      cudaGetLastError();   // variant not available on this grid (shared memory)
+      continue;
+    }
+    constexpr int kReps = 5;
+    if (!ck(c, cudaEventRecord(c->ev0, c->st), "autotune")) return false;
+    for (int r = 0; r < kReps; ++r)
+      if (!ck(c, launch_apply_gamma(g, in, out, c->spec, nullptr, GM_LINEAR, c->st), "autotune"))
+        return false;
+    float ms = 0.f;
+    if (!ck(c, cudaEventRecord(c->ev1, c->st), "autotune") ||
+        !ck(c, cudaEventSynchronize(c->ev1), "autotune") ||
+        !ck(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1), "autotune"))
+      return false;
+    if (ms < best) {
+      best = ms;
+      best_v = v;
+    }
+  }
+  c->g.pencil_t = c->gb.pencil_t = c->gp.pencil_t = best_v;
+  return true;
+}
 
 // Switch the reference medium C0 of the context (tables and Green operator).
 cudaError_t set_reference_medium(rpm_ctx* c, rpm_iso c0) {
@@ -323,6 +361,7 @@ void rpm_default_options(rpm_options* o) {
   o->warm_max_iters = 2000;
   o->warm_p_max = 0;
   o->warm_from_eps0 = 0;
+  o->autotune = 0;
 }
 
 int rpm_grid_supported(int nx, int ny, int nz) { return grid_supported(nx, ny, nz) ? 1 : 0; }
@@ -559,6 +598,7 @@ rpm_status rpm_create(const rpm_grid* grid, const uint8_t* phase, int phase_on_d
   }
   rpm_status s = rpm_set_phase(c, phase, phase_on_device);
   if (s == RPM_OK && cudaStreamSynchronize(c->st) != cudaSuccess) s = RPM_ERR_CUDA;
+  if (s == RPM_OK && o.autotune && !autotune_tiles(c)) s = RPM_ERR_CUDA;
   if (s != RPM_OK) {
     rpm_destroy(c);
     return s;
@@ -566,6 +606,8 @@ rpm_status rpm_create(const rpm_grid* grid, const uint8_t* phase, int phase_on_d
   *out = c;
   return RPM_OK;
 }
+
+int rpm_pencil_tile(const rpm_ctx* c) { return c ? pencil_tile(c->g) : 0; }
 
 rpm_status rpm_set_trace(rpm_ctx* c, double* residuals, int* basis_sizes, int capacity) {
   if (!c || capacity < 0) return fail(c, RPM_ERR_INVALID_ARG, "bad trace arguments");

@@ -36,6 +36,7 @@ struct GridDev {
   float lam0, mu0;
   float inv_lx, inv_ly, inv_lz;   // 1 / L_j (frequency scaling)
   int nyquist;           // 0: zero mixed Nyquist frequencies, 1: signed
+  int pencil_t;          // pass-B tile variant: 0 default, 1 half, 2 twice the pencils
 };
 
 // One Gamma0 application: in [6][n] -> out [6][n] through the spectrum
@@ -46,6 +47,7 @@ cudaError_t launch_apply_gamma(const GridDev& g, const float* in, float* out, fl
 
 bool grid_supported(int nx, int ny, int nz);
 int gamma_launches(int nx, int ny);   // kernels per Gamma0 application (3 or 5)
+int pencil_tile(const GridDev& g);    // pencils per pass-B block for g.pencil_t
 
 // ---- field kernels (field_kernels.cu) -------------------------------------
 // Partial sums per block, then one finishing block; see the definitions.

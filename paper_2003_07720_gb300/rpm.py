@@ -53,7 +53,7 @@ class rpm_options(ctypes.Structure):
                 ("scheme", ctypes.c_int), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
                 ("warm_tol", ctypes.c_double), ("warm_c0_scale", ctypes.c_double),
                 ("warm_max_iters", ctypes.c_int), ("warm_p_max", ctypes.c_int),
-                ("warm_from_eps0", ctypes.c_int)]
+                ("warm_from_eps0", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class rpm_solve_info(ctypes.Structure):
@@ -86,7 +86,8 @@ _lib = None
 EXPORTS = ("rpm_default_options", "rpm_create", "rpm_set_phase", "rpm_set_options",
            "rpm_apply_gamma", "rpm_solve", "rpm_effective_stiffness", "rpm_last_error",
            "rpm_status_string", "rpm_device_bytes", "rpm_grid_supported", "rpm_destroy",
-           "rpm_set_trace", "rpm_set_materials", "rpm_effective_stiffness_batch")
+           "rpm_set_trace", "rpm_set_materials", "rpm_effective_stiffness_batch",
+           "rpm_pencil_tile")
 
 
 def lib():
@@ -131,6 +132,8 @@ def lib():
                                                 ctypes.c_int, P(ctypes.c_double),
                                                 P(rpm_solve_info), P(ctypes.c_int)]
     L.rpm_effective_stiffness_batch.restype = ctypes.c_int
+    L.rpm_pencil_tile.argtypes = [vp]
+    L.rpm_pencil_tile.restype = ctypes.c_int
     L.rpm_destroy.argtypes = [vp]
     L.rpm_destroy.restype = None
     _lib = L
@@ -283,6 +286,11 @@ def rpm_effective_stiffness_batch(cells, options: rpm_options | None = None, n_w
         raise RpmError(st, "rpm_effective_stiffness_batch failed")
     return (np.array(C[:36 * n]).reshape(n, 6, 6), [[infos[6 * i + j].as_dict() for j in range(6)]
                                                    for i in range(n)], list(stat[:n]), st)
+
+
+def rpm_pencil_tile(ctx) -> int:
+    """Pencils per block of the z pass in use (the autotuner's choice)."""
+    return int(lib().rpm_pencil_tile(ctx))
 
 
 def rpm_device_bytes(ctx) -> int:

@@ -358,3 +358,21 @@ def test_ellipsoids_256_warm_form_converges_within_bounds(rpm):
     R = o.reuss_bound([1 - f1, f1], cell.lam, cell.mu)
     s = np.array(info["mean_stress"])
     assert R[0, 0] < s[0] < V[0, 0], (R[0, 0], s[0], V[0, 0])
+
+
+@pytest.mark.parametrize("n", [48, 128])
+def test_autotuned_tile_gives_identical_solve(rpm, n):
+    """The tile autotuner picks one of the z-pass variants (half, default or
+    twice the pencils per block); every pencil is transformed the same way
+    whatever the tile, so the solve is bit-identical to the default one."""
+    cell = ms.cell_nearvoid(n, 0, e_incl=1e-1) if n == 128 else ms.cell_batch_member(1)
+    E = ms.unit_strain(0)
+    with rpm.Context(cell, rpm.rpm_default_options()) as a:
+        t0 = rpm.rpm_pencil_tile(a.handle)
+        _, ia = a.solve(E)
+    with rpm.Context(cell, rpm.rpm_default_options(autotune=1)) as b:
+        t1 = rpm.rpm_pencil_tile(b.handle)
+        _, ib = b.solve(E)
+    assert t1 in (max(t0 // 2, 1), t0, 2 * t0), (t0, t1)
+    assert ia["converged"] and ib["converged"]
+    assert ia["mean_stress"] == ib["mean_stress"] and ia["iters"] == ib["iters"]
