@@ -117,6 +117,15 @@ rpm_status rpm_fno_features(const uint8_t* phase, long long n, int n_phases,
  * after eps0 is written (synchronises both streams). */
 rpm_status rpm_fno_warm_start(rpm_fno* f, rpm_ctx* ctx, const double E[6], float* eps0);
 
+/* rpm_solve from the learned warm start, with the cold start as the
+ * fallback: rpm_fno_warm_start, then rpm_solve from that guess; if that
+ * solve diverges or does not converge, rpm_solve again from eps0 = E (the
+ * context's own form).  Outputs and info as rpm_solve (info of the last
+ * solve, with the F applications, device time and launches of both);
+ * used_guess (optional) = 1 when the learned start's solve is the answer. */
+rpm_status rpm_fno_solve(rpm_fno* f, rpm_ctx* ctx, const double E[6], float* eps_out,
+                         float* sig_out, int out_on_host, rpm_solve_info* info, int* used_guess);
+
 size_t rpm_fno_device_bytes(const rpm_fno* f);
 const char* rpm_fno_last_error(const rpm_fno* f);
 void rpm_fno_destroy(rpm_fno* f);

@@ -947,6 +947,7 @@ struct rpm_fno {
   double* hloss = nullptr;    // pinned
   float* feat1 = nullptr;     // warm start: features and output of one sample
   float* out1 = nullptr;
+  float* eps0 = nullptr;      // rpm_fno_solve: the projected guess
   float2* ftab = nullptr;     // feature table per phase id (256)
   cudaEvent_t ev = nullptr;
   long long step = 0;
@@ -1099,6 +1100,7 @@ rpm_status rpm_fno_create(const rpm_fno_config* cfg, void* cuda_stream, rpm_fno*
       alloc((void**)&f->extra, 64) && alloc((void**)&f->Ed, B * CE * sizeof(float)) &&
       alloc((void**)&f->feat1, f->N3 * CV * sizeof(float)) &&
       alloc((void**)&f->out1, f->N3 * COUT * sizeof(float)) &&
+      alloc((void**)&f->eps0, f->N3 * COUT * sizeof(float)) &&
       alloc((void**)&f->ftab, 256 * sizeof(float2));
   if (!ok || cudaMallocHost((void**)&f->hE, B * CE * sizeof(float)) != cudaSuccess ||
       cudaMallocHost((void**)&f->hloss, 64) != cudaSuccess ||
@@ -1277,14 +1279,41 @@ rpm_status rpm_fno_warm_start(rpm_fno* f, rpm_ctx* ctx, const double E[6], float
   return RPM_OK;
 }
 
+rpm_status rpm_fno_solve(rpm_fno* f, rpm_ctx* ctx, const double E[6], float* eps_out,
+                         float* sig_out, int out_on_host, rpm_solve_info* info, int* used_guess) {
+  if (used_guess) *used_guess = 0;
+  rpm_status s = rpm_fno_warm_start(f, ctx, E, f ? f->eps0 : nullptr);
+  if (s != RPM_OK) return s;
+  rpm_solve_info first{};
+  s = rpm_solve(ctx, E, f->eps0, eps_out, sig_out, out_on_host, &first);
+  if (s == RPM_OK) {
+    if (used_guess) *used_guess = 1;
+    if (info) *info = first;
+    return RPM_OK;
+  }
+  if (s != RPM_ERR_DIVERGED && s != RPM_ERR_NOT_CONVERGED) {
+    if (info) *info = first;
+    return s;
+  }
+  // the cold start is the fallback: the context's own form from eps0 = E
+  rpm_solve_info second{};
+  s = rpm_solve(ctx, E, nullptr, eps_out, sig_out, out_on_host, &second);
+  second.gamma_applies += first.gamma_applies;
+  second.ms += first.ms;
+  second.launches += first.launches;
+  if (info) *info = second;
+  return s;
+}
+
 size_t rpm_fno_device_bytes(const rpm_fno* f) { return f ? f->bytes : 0; }
 
 const char* rpm_fno_last_error(const rpm_fno* f) { return f ? f->err.c_str() : "null network"; }
 
 void rpm_fno_destroy(rpm_fno* f) {
   if (!f) return;
-  void* dev[] = {f->params, f->grads, f->adam1, f->adam2, f->acts,  f->dvbuf, f->A2, f->Bz,
-                 f->Vs,     f->tw,    f->part,  f->extra, f->Ed,    f->feat1, f->out1, f->ftab};
+  void* dev[] = {f->params, f->grads, f->adam1, f->adam2, f->acts, f->dvbuf,
+                 f->A2,     f->Bz,    f->Vs,    f->tw,    f->part, f->extra,
+                 f->Ed,     f->feat1, f->out1,  f->eps0,  f->ftab};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (f->hE) cudaFreeHost(f->hE);

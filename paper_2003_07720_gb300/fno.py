@@ -33,7 +33,7 @@ class rpm_fno_adam(ctypes.Structure):
 
 EXPORTS = ("rpm_fno_param_count", "rpm_fno_create", "rpm_fno_set_params", "rpm_fno_get_params",
            "rpm_fno_get_grads", "rpm_fno_forward", "rpm_fno_loss_grad", "rpm_fno_adam_step",
-           "rpm_fno_train_step", "rpm_fno_features", "rpm_fno_warm_start",
+           "rpm_fno_train_step", "rpm_fno_features", "rpm_fno_warm_start", "rpm_fno_solve",
            "rpm_fno_device_bytes", "rpm_fno_last_error", "rpm_fno_destroy")
 
 _done = False
@@ -66,6 +66,9 @@ def lib():
     L.rpm_fno_features.restype = i
     L.rpm_fno_warm_start.argtypes = [vp, vp, P(ctypes.c_double), vp]
     L.rpm_fno_warm_start.restype = i
+    L.rpm_fno_solve.argtypes = [vp, vp, P(ctypes.c_double), vp, vp, i, P(rpm.rpm_solve_info),
+                                P(ctypes.c_int)]
+    L.rpm_fno_solve.restype = i
     L.rpm_fno_device_bytes.argtypes = [vp]
     L.rpm_fno_device_bytes.restype = ctypes.c_size_t
     L.rpm_fno_last_error.argtypes = [vp]
@@ -203,6 +206,18 @@ class Fno:
         """eps0 <- projected network guess for the context's cell and strain E."""
         handle = ctx.handle if hasattr(ctx, "handle") else ctx
         _ck(self.h, lib().rpm_fno_warm_start(self.h, handle, rpm._E(E), rpm._ptr(eps0)))
+
+    def solve(self, ctx, E, eps_out=None, sig_out=None, out_on_host=False):
+        """rpm_solve from the learned guess, falling back to the cold start;
+        returns (status, info dict, used_guess)."""
+        handle = ctx.handle if hasattr(ctx, "handle") else ctx
+        info = rpm.rpm_solve_info()
+        used = ctypes.c_int()
+        st = lib().rpm_fno_solve(self.h, handle, rpm._E(E), rpm._ptr(eps_out), rpm._ptr(sig_out),
+                                 int(out_on_host), ctypes.byref(info), ctypes.byref(used))
+        if st in (rpm.RPM_ERR_INVALID_ARG, rpm.RPM_ERR_CUDA):
+            _ck(self.h, st)
+        return st, info.as_dict(), bool(used.value)
 
     def device_bytes(self) -> int:
         return int(lib().rpm_fno_device_bytes(self.h))

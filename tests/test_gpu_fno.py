@@ -238,16 +238,24 @@ def test_trained_network_gain_is_measured(fno):
         hist = fno_train.train(net, data, epochs=30, batch=B, lr=4e-3)
         assert hist[-1] < 0.9 * hist[0], hist
         rows = fno_train.evaluate(net, N, list(range(5000, 5006)))
-    gains, failed = [], []
-    for r in rows:
-        if not r["cold"]["converged"]:
-            continue
-        if not r["learned"]["converged"]:
-            failed.append(r["seed"])
-            continue
-        a, b = np.array(r["cold"]["mean_stress"]), np.array(r["learned"]["mean_stress"])
-        assert np.max(np.abs(a - b)) < 1e-4 * np.max(np.abs(a)), r
-        gains.append(r["cold"]["F"] - r["learned"]["F"])
+        gains, failed = [], []
+        for r in rows:
+            if not r["cold"]["converged"]:
+                continue
+            if not r["learned"]["converged"]:
+                failed.append(r["seed"])
+                # rpm_fno_solve falls back to the cold start and reaches its answer
+                from paper_2003_07720_gb300 import rpm
+                cell = ms.cell_fno_member(r["seed"], N)
+                with rpm.Context(cell, rpm.rpm_default_options()) as ctx:
+                    st, info, used = net.solve(ctx, 0.01 * ms.strain_direction(r["seed"]))
+                assert st == rpm.RPM_OK and info["converged"] and not used, info
+                a = np.array(r["cold"]["mean_stress"])
+                assert np.max(np.abs(np.array(info["mean_stress"]) - a)) < 1e-4 * np.max(np.abs(a))
+                continue
+            a, b = np.array(r["cold"]["mean_stress"]), np.array(r["learned"]["mean_stress"])
+            assert np.max(np.abs(a - b)) < 1e-4 * np.max(np.abs(a)), r
+            gains.append(r["cold"]["F"] - r["learned"]["F"])
     assert gains, rows
     print("F saved by the learned start per held-out cell:", gains,
           "; learned starts that did not converge (cold did):", failed)
