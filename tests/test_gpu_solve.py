@@ -254,6 +254,26 @@ def test_softincl128_warm_solve_matches_oracle_golden(rpm):
     assert abs(info["gamma_applies"] - ref["f_applies"]) <= 12
 
 
+def test_softincl128_cold_solve_matches_oracle_golden(rpm):
+    """The cold form of the benchmark (RPM on Eq. 3.9 from eps = E, C0 = matrix)
+    at full size against the oracle's own converged solve of the same form
+    (tests/golden/nearvoid128_oracle_solve.json, written by
+    tests/golden/make_golden.py from the oracle only; hours of FP64 work)."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "nearvoid128_oracle_solve.json")
+    if not os.path.exists(path):
+        pytest.skip("cold-form oracle solve not stored")
+    ref = json.load(open(path))
+    cell = ms.cell_nearvoid(128, 0, c0_scale=1.0, e_incl=1e-3)
+    with rpm.Context(cell, rpm.rpm_default_options(tol=1e-6, p_max=20)) as ctx:
+        st, info = ctx.solve(ms.unit_strain(0))
+    assert info["converged"]
+    sig = np.array(info["mean_stress"])
+    sref = np.array(ref["mean_stress"])
+    assert np.max(np.abs(sig - sref)) < CEFF_TOL * np.max(np.abs(sref)), (sig, sref)
+
+
 def test_warm_started_solve_matches_cold(rpm, sphere32):
     """Warm start by the Accelerated scheme (Algorithm 3) followed by RPM on
     Eq. 3.9: same converged result as the cold start, within tolerance."""
