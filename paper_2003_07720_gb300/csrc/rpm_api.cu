@@ -842,9 +842,6 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
       status = RPM_ERR_NOT_CONVERGED;
       break;
     }
-    // Without a basis the steps need no host decision between them: run up to
-    // kBatch of them back to back and test the residual of the last one only
-    // (never past a basis-growth point or max_iters).
     // Steps between host reads of the residual: up to kBatch while the basis
     // is empty, and with a basis while the residual is still far (> 100 tol)
     // from the test and no residual history is recorded, never past a
