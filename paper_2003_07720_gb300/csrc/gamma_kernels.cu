@@ -334,6 +334,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(GridDev g, float2* __restri
 // ---------------------------------------------------------------------------
 constexpr int kRows = 32;             // rows per block in the x passes
 constexpr int kRowsP = kRows + 1;     // odd stride
+constexpr int RowsFwdLoads = 4;       // loads in flight per thread in k_rows_fwd
 
 template <int NX>
 __global__ void __launch_bounds__(kThreads) k_rows_fwd(GridDev g, const float* __restrict__ in,
@@ -356,27 +357,49 @@ __global__ void __launch_bounds__(kThreads) k_rows_fwd(GridDev g, const float* _
   const size_t row2 = ((size_t)z * ny + y0) * NXH;         // float2 offset of row y0
   const float2* in2 = reinterpret_cast<const float2*>(in);
   const uchar2* ph2 = reinterpret_cast<const uchar2*>(g.phase) + row2;
-  constexpr int TOT = kRows * NXH;
-  for (int idx = threadIdx.x; idx < TOT; idx += kThreads) {
-    const int r = idx / NXH, h = idx - r * NXH;
-    float2 t = make_float2(0.f, 0.f);
-    if (y0 + r < ny) {
-      const size_t v = row2 + idx;
-      if (mode == GM_RAW_TAU) {
-        t = in2[c * n2 + v];
-      } else {
-        const uchar2 ph = ph2[idx];
-        const float2 d0 = dm[ph.x], d1 = dm[ph.y];
-        const float2 e = in2[c * n2 + v];
-        t = make_float2(2.f * d0.y * e.x, 2.f * d1.y * e.y);
-        if (c < 3) {
-          const float2 a = in2[v], b = in2[n2 + v], d = in2[2 * n2 + v];
-          t.x = fmaf(d0.x, a.x + b.x + d.x, t.x);
-          t.y = fmaf(d1.x, a.y + b.y + d.y, t.y);
+  // Loads are issued in groups of U per thread before any use (several
+  // independent requests in flight per thread, as in pass A).
+  constexpr int TOT = kRows * NXH, U = RowsFwdLoads;
+  for (int base = threadIdx.x; base < TOT; base += U * kThreads) {
+    float2 e[U], a[U], b[U], d[U];
+    uchar2 ph[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * kThreads;
+      if (idx < TOT && y0 + idx / NXH < ny) {
+        const size_t v = row2 + idx;
+        e[u] = in2[c * n2 + v];
+        if (mode != GM_RAW_TAU) {
+          ph[u] = ph2[idx];
+          if (c < 3) {
+            a[u] = in2[v];
+            b[u] = in2[n2 + v];
+            d[u] = in2[2 * n2 + v];
+          }
         }
       }
     }
-    P[h * kRowsP + r] = t;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * kThreads;
+      if (idx < TOT) {
+        const int r = idx / NXH, h = idx - r * NXH;
+        float2 t = make_float2(0.f, 0.f);
+        if (y0 + r < ny) {
+          if (mode == GM_RAW_TAU) {
+            t = e[u];
+          } else {
+            const float2 d0 = dm[ph[u].x], d1 = dm[ph[u].y];
+            t = make_float2(2.f * d0.y * e[u].x, 2.f * d1.y * e[u].y);
+            if (c < 3) {
+              t.x = fmaf(d0.x, a[u].x + b[u].x + d[u].x, t.x);
+              t.y = fmaf(d1.x, a[u].y + b[u].y + d[u].y, t.y);
+            }
+          }
+        }
+        P[h * kRowsP + r] = t;
+      }
+    }
   }
   __syncthreads();
   smem_fft<NXH, false, kRows, 1, kRowsP>(P, twx);
