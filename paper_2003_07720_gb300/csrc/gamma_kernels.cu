@@ -334,20 +334,26 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(GridDev g, float2* __restri
 // ---------------------------------------------------------------------------
 constexpr int kRows = 32;             // rows per block in the x passes
 constexpr int kRowsP = kRows + 1;     // odd stride
-constexpr int RowsFwdLoads = 4;       // loads in flight per thread in k_rows_fwd
+
+// Forward x pass of the five-pass variant, one block per (component group,
+// group of kRowsG rows, z): group 0 holds the three normal components, group 1
+// the three shear components, as 3 kRowsG lines.  Each strain component is
+// loaded once and the trace once per voxel (Eq. 2.3), then the packed
+// half-length x-FFT and the real-to-complex untangling run on all lines.
+constexpr int kRowsG = 16;              // rows of one component per block
+constexpr int kLinesG = 3 * kRowsG;     // lines per block (three components)
+constexpr int kLinesGP = kLinesG + 1;   // odd stride
 
 template <int NX>
 __global__ void __launch_bounds__(kThreads) k_rows_fwd(GridDev g, const float* __restrict__ in,
                                                        float2* __restrict__ spec, int mode) {
   constexpr int NXH = NX / 2, SX = NXH + 1;
   extern __shared__ float2 sm[];
-  float2* P = sm;                                  // [SX][kRowsP]
-  float2* twx = P + SX * kRowsP;
+  float2* P = sm;                                  // [SX][kLinesGP], line = j kRowsG + row
+  float2* twx = P + SX * kLinesGP;
   float2* r2c = twx + NXH;
   float2* dm = r2c + SX;
-  // component fastest: the blocks of one row block run together and share the
-  // normal components through L2
-  const int c = blockIdx.x, y0 = blockIdx.y * kRows, z = blockIdx.z;
+  const int grp = blockIdx.x, y0 = blockIdx.y * kRowsG, z = blockIdx.z;
   const int ny = g.ny;
   for (int i = threadIdx.x; i < NXH; i += blockDim.x) twx[i] = g.tw_x[i];
   for (int i = threadIdx.x; i < SX; i += blockDim.x) r2c[i] = g.r2c_w[i];
@@ -355,28 +361,20 @@ __global__ void __launch_bounds__(kThreads) k_rows_fwd(GridDev g, const float* _
   __syncthreads();
   const size_t n2 = (size_t)g.n / 2;
   const size_t row2 = ((size_t)z * ny + y0) * NXH;         // float2 offset of row y0
-  const float2* in2 = reinterpret_cast<const float2*>(in);
+  const float2* in2 = reinterpret_cast<const float2*>(in) + 3 * grp * n2 + row2;
   const uchar2* ph2 = reinterpret_cast<const uchar2*>(g.phase) + row2;
-  // Loads are issued in groups of U per thread before any use (several
-  // independent requests in flight per thread, as in pass A).
-  constexpr int TOT = kRows * NXH, U = RowsFwdLoads;
+  // Loads are issued in groups of U voxel pairs per thread before any use.
+  constexpr int TOT = kRowsG * NXH, U = 2;
   for (int base = threadIdx.x; base < TOT; base += U * kThreads) {
-    float2 e[U], a[U], b[U], d[U];
+    float2 e[U][3];
     uchar2 ph[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int idx = base + u * kThreads;
       if (idx < TOT && y0 + idx / NXH < ny) {
-        const size_t v = row2 + idx;
-        e[u] = in2[c * n2 + v];
-        if (mode != GM_RAW_TAU) {
-          ph[u] = ph2[idx];
-          if (c < 3) {
-            a[u] = in2[v];
-            b[u] = in2[n2 + v];
-            d[u] = in2[2 * n2 + v];
-          }
-        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) e[u][j] = in2[j * n2 + idx];
+        if (mode != GM_RAW_TAU) ph[u] = ph2[idx];
       }
     }
 #pragma unroll
@@ -384,44 +382,57 @@ __global__ void __launch_bounds__(kThreads) k_rows_fwd(GridDev g, const float* _
       const int idx = base + u * kThreads;
       if (idx < TOT) {
         const int r = idx / NXH, h = idx - r * NXH;
-        float2 t = make_float2(0.f, 0.f);
+        float2 t[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) t[j] = make_float2(0.f, 0.f);
         if (y0 + r < ny) {
           if (mode == GM_RAW_TAU) {
-            t = e[u];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) t[j] = e[u][j];
           } else {
             const float2 d0 = dm[ph[u].x], d1 = dm[ph[u].y];
-            t = make_float2(2.f * d0.y * e[u].x, 2.f * d1.y * e[u].y);
-            if (c < 3) {
-              t.x = fmaf(d0.x, a[u].x + b[u].x + d[u].x, t.x);
-              t.y = fmaf(d1.x, a[u].y + b[u].y + d[u].y, t.y);
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+              t[j] = make_float2(2.f * d0.y * e[u][j].x, 2.f * d1.y * e[u][j].y);
+            if (grp == 0) {
+              const float trx = e[u][0].x + e[u][1].x + e[u][2].x;
+              const float try_ = e[u][0].y + e[u][1].y + e[u][2].y;
+#pragma unroll
+              for (int j = 0; j < 3; ++j) {
+                t[j].x = fmaf(d0.x, trx, t[j].x);
+                t[j].y = fmaf(d1.x, try_, t[j].y);
+              }
             }
           }
         }
-        P[h * kRowsP + r] = t;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) P[h * kLinesGP + j * kRowsG + r] = t[j];
       }
     }
   }
   __syncthreads();
-  smem_fft<NXH, false, kRows, 1, kRowsP>(P, twx);
-  for (int t = threadIdx.x; t < kRows * (NXH / 2 + 1); t += blockDim.x) {
-    const int r = t % kRows, k = t / kRows;
+  smem_fft<NXH, false, kLinesG, 1, kLinesGP>(P, twx);
+  for (int t = threadIdx.x; t < kLinesG * (NXH / 2 + 1); t += blockDim.x) {
+    const int r = t % kLinesG, k = t / kLinesG;
     if (k == 0) {
       const float2 z0 = P[r];
       P[r] = make_float2(z0.x + z0.y, 0.f);
-      P[NXH * kRowsP + r] = make_float2(z0.x - z0.y, 0.f);
+      P[NXH * kLinesGP + r] = make_float2(z0.x - z0.y, 0.f);
     } else {
       const int kk = NXH - k;
       const int sk = slot_of<NXH>(k), skk = slot_of<NXH>(kk);
-      const float2 a = P[sk * kRowsP + r], b = P[skk * kRowsP + r];
-      P[sk * kRowsP + r] = r2c_post(a, b, r2c[k]);
-      if (kk != k) P[skk * kRowsP + r] = r2c_post(b, a, r2c[kk]);
+      const float2 a = P[sk * kLinesGP + r], b = P[skk * kLinesGP + r];
+      P[sk * kLinesGP + r] = r2c_post(a, b, r2c[k]);
+      if (kk != k) P[skk * kLinesGP + r] = r2c_post(b, a, r2c[kk]);
     }
   }
   __syncthreads();
-  float2* out = spec + ((size_t)c * g.nz + z) * g.plane + (size_t)y0 * SX;
-  for (int idx = threadIdx.x; idx < kRows * SX; idx += blockDim.x) {
-    const int r = idx / SX, sx = idx - r * SX;
-    if (y0 + r < ny) out[idx] = P[sx * kRowsP + r];
+  for (int idx = threadIdx.x; idx < kLinesG * SX; idx += blockDim.x) {
+    const int l = idx / SX, sx = idx - l * SX;
+    const int j = l / kRowsG, r = l - j * kRowsG;
+    if (y0 + r < ny)
+      spec[((size_t)(3 * grp + j) * g.nz + z) * g.plane + (size_t)(y0 + r) * SX + sx] =
+          P[sx * kLinesGP + l];
   }
 }
 
@@ -554,10 +565,11 @@ static cudaError_t launch_rows(const GridDev& g, const float* in, float* out, fl
   constexpr int NXH = NX / 2, SX = NXH + 1;
   const dim3 grid(6, (g.ny + kRows - 1) / kRows, g.nz);
   if (which == 0) {
-    const size_t smem = (size_t)(SX * kRowsP + NXH + SX + 256) * sizeof(float2);
+    const dim3 grid_f(2, (g.ny + kRowsG - 1) / kRowsG, g.nz);
+    const size_t smem = (size_t)(SX * kLinesGP + NXH + SX + 256) * sizeof(float2);
     cudaError_t e = set_smem(k_rows_fwd<NX>, smem);
     if (e != cudaSuccess) return e;
-    k_rows_fwd<NX><<<grid, kThreads, smem, st>>>(g, in, spec, mode);
+    k_rows_fwd<NX><<<grid_f, kThreads, smem, st>>>(g, in, spec, mode);
   } else {
     const size_t smem = (size_t)(SX * kRowsP + NXH + SX) * sizeof(float2);
     cudaError_t e = set_smem(k_rows_inv<NX>, smem);
