@@ -243,9 +243,12 @@ __device__ __forceinline__ void green_apply(float2* t, float n1, float n2, float
   t[5] = make_float2(-0.5f * (n1 * w2.x + n2 * w1.x), -0.5f * (n1 * w2.y + n2 * w1.y));
 }
 
-template <int NZ, int TT>
-__global__ void __launch_bounds__(kThreads) k_pass_b(GridDev g, float2* __restrict__ spec, int mode,
-                                                     GammaArgs ga) {
+// Pass B body for NT threads per block (k_pass_b: 256; k_pass_b_wide: 512,
+// where shared memory limits a block of 256 to two blocks per SM, nz >= 256,
+// so that 32 warps per SM hide the latency).
+template <int NZ, int TT, int NT>
+__device__ __forceinline__ void pass_b_body(const GridDev& g, float2* __restrict__ spec, int mode,
+                                            const GammaArgs& ga) {
   using C = PencilCfg<NZ, TT>;
   constexpr int T = C::T, NZP = C::NZP;
   extern __shared__ float2 sm[];
@@ -269,11 +272,11 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(GridDev g, float2* __restri
   }
   {
     constexpr int TOT = 6 * NZ * T, U = 8;
-    for (int base = threadIdx.x; base < TOT; base += U * kThreads) {
+    for (int base = threadIdx.x; base < TOT; base += U * NT) {
       float2 v[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int idx = base + u * kThreads;
+        const int idx = base + u * NT;
         const int t = idx % T, r = idx / T, z = r % NZ, c = r / NZ;
         const int m = m0 + t;
         v[u] = (idx < TOT && m < plane) ? spec[((size_t)c * NZ + z) * plane + m]
@@ -281,7 +284,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(GridDev g, float2* __restri
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int idx = base + u * kThreads;
+        const int idx = base + u * NT;
         if (idx < TOT) {
           const int t = idx % T, r = idx / T, z = r % NZ, c = r / NZ;
           B[(c * T + t) * NZP + z] = v[u];
@@ -324,6 +327,19 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(GridDev g, float2* __restri
     const int m = m0 + t;
     if (m < plane) spec[((size_t)c * NZ + z) * plane + m] = B[(c * T + t) * NZP + z];
   }
+}
+
+template <int NZ, int TT>
+__global__ void __launch_bounds__(kThreads) k_pass_b(GridDev g, float2* __restrict__ spec, int mode,
+                                                     GammaArgs ga) {
+  pass_b_body<NZ, TT, kThreads>(g, spec, mode, ga);
+}
+
+template <int NZ, int TT>
+__global__ void __launch_bounds__(2 * kThreads, 2) k_pass_b_wide(GridDev g,
+                                                                float2* __restrict__ spec,
+                                                                int mode, GammaArgs ga) {
+  pass_b_body<NZ, TT, 2 * kThreads>(g, spec, mode, ga);
 }
 
 // ---------------------------------------------------------------------------
@@ -540,10 +556,15 @@ static cudaError_t launch_pencil_tile(const GridDev& g, float2* spec, int mode,
   using C = PencilCfg<NZ, TT>;
   const size_t smem = (size_t)(6 * C::T * C::NZP + NZ) * sizeof(float2);
   if (TT < 1 || smem > 227 * 1024) return cudaErrorInvalidValue;   // variant not available
-  cudaError_t e = set_smem(k_pass_b<NZ, TT>, smem);
-  if (e != cudaSuccess) return e;
   const int blocks = (g.plane + C::T - 1) / C::T;
-  k_pass_b<NZ, TT><<<blocks, kThreads, smem, st>>>(g, spec, mode, ga);
+  cudaError_t e;
+  if constexpr (NZ >= 256 && C::T >= 8) {
+    if ((e = set_smem(k_pass_b_wide<NZ, TT>, smem)) != cudaSuccess) return e;
+    k_pass_b_wide<NZ, TT><<<blocks, 2 * kThreads, smem, st>>>(g, spec, mode, ga);
+  } else {
+    if ((e = set_smem(k_pass_b<NZ, TT>, smem)) != cudaSuccess) return e;
+    k_pass_b<NZ, TT><<<blocks, kThreads, smem, st>>>(g, spec, mode, ga);
+  }
   return cudaGetLastError();
 }
 
