@@ -6,7 +6,6 @@ import itertools
 import math
 
 import numpy as np
-import pytest
 
 import microstructure as ms
 
@@ -75,8 +74,8 @@ def test_rsa_spheres_are_disjoint_and_stamped_exactly():
         d = c1 - c2
         d -= n * np.round(d / n)
         assert math.sqrt(float(d @ d)) >= r1 + r2
-    # the map is the union of the listed spheres; centres are (x, y, z) in voxels,
-    # the map is indexed [z, y, x]
+    # the map is the union of the listed spheres (centres stored as (z, y, x)
+    # in voxel units)
     union = _brute_union(n, [((c[2], c[1], c[0]), r) for c, r in spheres])
     assert np.array_equal(mask.astype(bool), union)
     # stops at the first sphere that reaches the target
