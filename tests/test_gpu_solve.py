@@ -265,6 +265,8 @@ def test_softincl128_cold_solve_matches_oracle_golden(rpm):
     if not os.path.exists(path):
         pytest.skip("cold-form oracle solve not stored")
     ref = json.load(open(path))
+    if ref["status"] != "ok":
+        pytest.skip(f"stored cold-form oracle solve did not converge ({ref['status']})")
     cell = ms.cell_nearvoid(128, 0, c0_scale=1.0, e_incl=1e-3)
     with rpm.Context(cell, rpm.rpm_default_options(tol=1e-6, p_max=20)) as ctx:
         st, info = ctx.solve(ms.unit_strain(0))
