@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(2 * kThreads, 2) k_pass_b_wide(GridDev g,
 // along y (inverse), rows along x (inverse).  The spectrum layout and slot
 // orders are those of the three-pass path, so pass B is shared.
 // ---------------------------------------------------------------------------
-constexpr int kRows = 32;             // rows per block in the x passes
+constexpr int kRows = 32;             // rows per block in the inverse x pass
 constexpr int kRowsP = kRows + 1;     // odd stride
 
 // Forward x pass of the five-pass variant, one block per (component group,
