@@ -1,7 +1,10 @@
 """Write the stored oracle results used by the GPU tests and the benchmark's
 reference arm.  Calls only oracle/ (and the seeded input generators).
 
-  python tests/golden/make_golden.py softincl128    # ~2-3 h on one core
+  python tests/golden/make_golden.py softincl128_warm   # ~10 min on one core
+  python tests/golden/make_golden.py stiff64            # ~7 min on one core
+  python tests/golden/make_golden.py softincl128        # cold form: more than 4 h
+                                                        # on one core (not stored)
 """
 from __future__ import annotations
 
