@@ -536,3 +536,57 @@ def test_stored_cold_and_warm_oracle_solves_agree():
     k_r = 1.0 / np.sum(w / (cell.lam + 2 * cell.mu / 3))
     g_r = 1.0 / np.sum(w / cell.mu)
     assert sc[0] >= k_r + 4 * g_r / 3
+
+
+@pytest.mark.parametrize("ratio,n_added", [(0.05, 1), (0.3, 2)])
+def test_growth_rule_adds_one_or_two_columns_by_the_qr_ratio(ratio, n_added):
+    """Eq. 3.8 on hand-built increments: with d1 = xi^nu - xi^(nu-1) = a and
+    d2 = xi^(nu-1) - xi^(nu-2) = b orthogonal to a, the QR factors are
+    T11 = |a|, T12 = 0, T22 = |b|; the rule keeps q1 = a/|a| alone when
+    |T22| <= kappa |T11| and both q1 and q2 = b/|b| otherwise, and H is
+    Z^T F_u Z for the vectors kept."""
+    prob = _prob((4, 4, 4), seed=2)
+    rng = _rng(11)
+    a = rng.standard_normal((6, 4, 4, 4))
+    b = rng.standard_normal((6, 4, 4, 4))
+    b -= o.inner(a, b) / o.inner(a, a) * a
+    b *= ratio * o.norm(a) / o.norm(b)
+    x0 = rng.standard_normal((6, 4, 4, 4))
+    hist = [x0, x0 + b, x0 + b + a]
+    st = o.RPMState([], [], np.zeros((0, 0)))
+    opts = o.Options(kappa=0.1, p_max=20)
+    assert o._grow_basis(prob, st, hist, opts) == n_added
+    assert len(st.Z) == n_added
+    assert np.allclose(st.Z[0], a / o.norm(a), atol=1e-12)
+    if n_added == 2:
+        assert np.allclose(st.Z[1], b / o.norm(b), atol=1e-12)
+    for i in range(n_added):
+        fu = o.apply_F_linear(prob, st.Z[i])
+        for j in range(n_added):
+            assert math.isclose(st.H[j, i], o.inner(st.Z[j], fu), rel_tol=1e-12, abs_tol=1e-12)
+
+
+def test_growth_projects_out_the_existing_basis_and_respects_p_max():
+    """With a basis Z already present, the increments are first projected
+    onto its orthogonal complement (the Q of Eq. 3.8), so an increment
+    inside span Z adds nothing; and no column is added beyond p_max."""
+    prob = _prob((4, 4, 4), seed=2)
+    rng = _rng(12)
+    e = rng.standard_normal((6, 4, 4, 4))
+    e /= o.norm(e)
+    st = o.RPMState([e], [o.apply_F_linear(prob, e)], np.zeros((1, 1)))
+    x0 = rng.standard_normal((6, 4, 4, 4))
+    hist = [x0, x0 + 2.0 * e, x0 + 5.0 * e]          # both increments inside span Z
+    assert o._grow_basis(prob, st, hist, o.Options()) == 0 and len(st.Z) == 1
+    a = rng.standard_normal((6, 4, 4, 4))
+    b = rng.standard_normal((6, 4, 4, 4))
+    hist = [x0, x0 + b + 3.0 * e, x0 + b + a - e]
+    assert o._grow_basis(prob, st, hist, o.Options(p_max=2)) == 1    # capped at p_max
+    Z = np.array([z.ravel() for z in st.Z])
+    w = np.tile(np.repeat([1.0, 1.0, 1.0, 2.0, 2.0, 2.0], 64), 1)
+    G = (Z * w) @ Z.T
+    assert np.allclose(G, np.eye(2), atol=1e-12)
+    # the new column is the normalised part of a - 4e orthogonal to e
+    d1 = a - 4.0 * e
+    d1 -= o.inner(e, d1) * e
+    assert np.allclose(st.Z[1], d1 / o.norm(d1), atol=1e-12)
