@@ -590,3 +590,26 @@ def test_growth_projects_out_the_existing_basis_and_respects_p_max():
     d1 = a - 4.0 * e
     d1 -= o.inner(e, d1) * e
     assert np.allclose(st.Z[1], d1 / o.norm(d1), atol=1e-12)
+
+
+@pytest.mark.parametrize("m", [(1, 2, 0), (0, 0, 3), (2, 1, 1)])
+def test_equilibrium_error_of_a_single_mode_closed_form(m):
+    """Algorithm 1's error for sigma(x) = sigma0 + S cos(2 pi m . x) on a unit
+    cell (x along the last axis): the only non-zero frequencies are +-m with
+    sigma_hat = S/2 each (after the 1/n normalisation), so the error is
+    sqrt(2 |S (2 pi m) / 2|^2) / |sigma0| = |S xi_m| / (sqrt(2) |sigma0|),
+    whichever half of the spectrum stores +-m."""
+    n = 8
+    prob = _prob((n, n, n), seed=1)
+    rng = _rng(21)
+    s0 = rng.standard_normal(6)
+    S6 = rng.standard_normal(6)
+    c = np.arange(n) / n
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    phase = 2 * math.pi * (m[0] * x + m[1] * y + m[2] * z)
+    sig = s0[:, None, None, None] + S6[:, None, None, None] * np.cos(phase)[None]
+    S = o.to_full(S6)
+    xi = 2 * math.pi * np.array(m, float)
+    s0_norm = math.sqrt(float(np.sum(np.array([1, 1, 1, 2, 2, 2]) * s0 * s0)))
+    expect = np.linalg.norm(S @ xi) / (math.sqrt(2.0) * s0_norm)
+    assert math.isclose(o.equilibrium_error(prob, sig), expect, rel_tol=1e-12)
