@@ -613,3 +613,32 @@ def test_equilibrium_error_of_a_single_mode_closed_form(m):
     s0_norm = math.sqrt(float(np.sum(np.array([1, 1, 1, 2, 2, 2]) * s0 * s0)))
     expect = np.linalg.norm(S @ xi) / (math.sqrt(2.0) * s0_norm)
     assert math.isclose(o.equilibrium_error(prob, sig), expect, rel_tol=1e-12)
+
+
+def test_bound_helpers_against_independent_results():
+    """The bound helpers used by the C_eff pins: the isotropic projection of an
+    isotropic stiffness returns its own K = lambda + 2 mu / 3 and G = mu; the
+    Hashin-Shtrikman bounds collapse to a phase at f = 0 and 1, are ordered
+    between the Reuss and Voigt averages, and for equal shear moduli both
+    bulk bounds equal Hill's exact result
+    1 / (K* + 4G/3) = f1 / (K1 + 4G/3) + f2 / (K2 + 4G/3)."""
+    for lam, mu in [(0.6, 0.4), (3.0, 1.2), (1e-3, 2e-3)]:
+        K, G = o.isotropic_projection(o.voigt_matrix(lam, mu))
+        assert math.isclose(K, lam + 2 * mu / 3, rel_tol=1e-13)
+        assert math.isclose(G, mu, rel_tol=1e-13)
+    K1, G1, K2, G2 = 1.0, 0.5, 20.0, 7.0
+    assert np.allclose(o.hashin_shtrikman(1.0, K1, G1, K2, G2), (K1, K1, G1, G1), rtol=1e-13)
+    assert np.allclose(o.hashin_shtrikman(0.0, K1, G1, K2, G2), (K2, K2, G2, G2), rtol=1e-13)
+    for f1 in (0.1, 0.4, 0.8):
+        Kl, Ku, Gl, Gu = o.hashin_shtrikman(f1, K1, G1, K2, G2)
+        f2 = 1 - f1
+        assert 1 / (f1 / K1 + f2 / K2) <= Kl <= Ku <= f1 * K1 + f2 * K2
+        assert 1 / (f1 / G1 + f2 / G2) <= Gl <= Gu <= f1 * G1 + f2 * G2
+        G = 0.9                          # (the shear terms need G2 != G1)
+        Kl, Ku, _, _ = o.hashin_shtrikman(f1, K1, G, K2, G * (1 + 1e-12))
+        hill = 1 / (f1 / (K1 + 4 * G / 3) + f2 / (K2 + 4 * G / 3)) - 4 * G / 3
+        assert math.isclose(Kl, hill, rel_tol=1e-9) and math.isclose(Ku, hill, rel_tol=1e-9)
+    # the Reuss and Voigt averages of one phase are its stiffness
+    C = o.voigt_matrix(1.3, 0.7)
+    assert np.allclose(o.reuss_bound([1.0], [1.3], [0.7]), C, rtol=1e-13)
+    assert np.allclose(o.voigt_bound([0.3, 0.7], [1.3, 1.3], [0.7, 0.7]), C, rtol=1e-13)
