@@ -642,3 +642,25 @@ def test_bound_helpers_against_independent_results():
     C = o.voigt_matrix(1.3, 0.7)
     assert np.allclose(o.reuss_bound([1.0], [1.3], [0.7]), C, rtol=1e-13)
     assert np.allclose(o.voigt_bound([0.3, 0.7], [1.3, 1.3], [0.7, 0.7]), C, rtol=1e-13)
+
+
+def test_laminate_closed_form_matches_backus_averages():
+    """Layers normal to e3 give a transversely isotropic C_eff whose entries
+    are Backus's averages of the layer moduli (M = lambda + 2 mu):
+    C33 = <1/M>^-1, C13 = <lambda/M> <1/M>^-1, C66 = <mu>, C44 = <1/mu>^-1,
+    C11 = <4 mu (lambda + mu) / M> + <lambda/M>^2 <1/M>^-1, C12 = C11 - 2 C66."""
+    f = np.array([0.25, 0.45, 0.30])
+    lam = np.array([ms.lame(1, 0.3)[0], ms.lame(40, 0.25)[0], ms.lame(1e-3, 0.3)[0]])
+    mu = np.array([ms.lame(1, 0.3)[1], ms.lame(40, 0.25)[1], ms.lame(1e-3, 0.3)[1]])
+    C = o.laminate_ceff(f, lam, mu)
+    M = lam + 2 * mu
+    avg = lambda v: float(np.sum(f * v))          # noqa: E731
+    c33 = 1 / avg(1 / M)
+    c13 = avg(lam / M) * c33
+    c66 = avg(mu)
+    c44 = 1 / avg(1 / mu)
+    c11 = avg(4 * mu * (lam + mu) / M) + avg(lam / M) ** 2 * c33
+    c12 = c11 - 2 * c66
+    ref = np.array([[c11, c12, c13, 0, 0, 0], [c12, c11, c13, 0, 0, 0], [c13, c13, c33, 0, 0, 0],
+                    [0, 0, 0, c44, 0, 0], [0, 0, 0, 0, c44, 0], [0, 0, 0, 0, 0, c66]])
+    assert np.allclose(C, ref, rtol=1e-12, atol=1e-14 * np.max(np.abs(ref)))
