@@ -33,3 +33,15 @@ def test_recorded_traffic_is_gated_by_the_kernel_sources():
     # the record matches the current sources (it is re-keyed with every capture)
     assert bench.recorded_traffic("gamma_apply_128") is not None
     assert bench.recorded_traffic("no_such_kernel") is None
+
+
+def test_cold_form_error_falls_back_to_the_same_fixed_point():
+    """Without a stored cold-form oracle solve, the cold form is compared with
+    the oracle's warm-form solve of the same cell (same fixed point of F)."""
+    import json
+    import os
+    ref = json.load(open(os.path.join(bench.ROOT, "tests", "golden",
+                                      "softincl128_warm_oracle_solve.json")))["mean_stress"]
+    e = bench.oracle_error("cold", ref)
+    assert e is not None and e["mean_stress_max_rel"] == 0.0
+    assert e["reference"].endswith(".json")
