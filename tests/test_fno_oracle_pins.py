@@ -155,3 +155,26 @@ def test_features_closed_form():
     li, mi = lame(100.0, 0.25)
     f = fo.features(np.array([[[0, 1]]]), [lm, li], [mm, mi])
     assert np.allclose(f[0].ravel(), [0.0, 2.0]) and np.allclose(f[1].ravel(), [0.3, 0.25])
+
+
+def test_adam_constant_gradient_steps_by_lr_every_step():
+    """With a constant gradient the bias-corrected moments are exactly g and
+    g^2 at every step t (m_t = (1 - b1^t) g, v_t = (1 - b2^t) g^2), so each
+    step moves by lr * sign(g)."""
+    g = np.array([0.7, -3.0, 2e-4])
+    p, m1, m2 = np.zeros(3), np.zeros(3), np.zeros(3)
+    for t in range(1, 6):
+        p, m1, m2 = fo.adam_step(p, g, m1, m2, t, lr=0.01, eps=0.0)
+        assert np.allclose(p, -0.01 * t * np.sign(g), rtol=1e-12, atol=0)
+        assert np.allclose(m1, (1 - 0.9 ** t) * g, rtol=1e-12)
+        assert np.allclose(m2, (1 - 0.999 ** t) * g * g, rtol=1e-12)
+
+
+def test_adam_weight_decay_is_decoupled():
+    """With zero gradient the moments stay zero and decoupled weight decay
+    alone shrinks the parameters geometrically: p_t = (1 - lr wd)^t p_0."""
+    p0 = np.array([1.5, -0.2, 4.0])
+    p, m1, m2 = p0.copy(), np.zeros(3), np.zeros(3)
+    for t in range(1, 4):
+        p, m1, m2 = fo.adam_step(p, np.zeros(3), m1, m2, t, lr=0.05, wd=0.1)
+    assert np.allclose(p, (1 - 0.05 * 0.1) ** 3 * p0, rtol=1e-13)
