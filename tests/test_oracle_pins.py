@@ -631,3 +631,30 @@ def test_laminate_closed_form_matches_backus_averages():
     ref = np.array([[c11, c12, c13, 0, 0, 0], [c12, c11, c13, 0, 0, 0], [c13, c13, c33, 0, 0, 0],
                     [0, 0, 0, c44, 0, 0], [0, 0, 0, 0, c44, 0], [0, 0, 0, 0, 0, c66]])
     assert np.allclose(C, ref, rtol=1e-12, atol=1e-14 * np.max(np.abs(ref)))
+
+
+def test_tensor_helpers_stress_and_polarization_by_independent_routes():
+    """The stored-component helpers against full 3x3 tensors: inner() is the
+    Frobenius contraction of the full tensors; stress() equals the full
+    fourth-order contraction C_ijkl eps_kl of each phase and the Voigt matrix
+    applied to engineering strains; polarization() is stress() with C - C0."""
+    prob = _prob((2, 3, 4), seed=5, c_ratio=(1.0, 7.0), vf=0.5)
+    rng = _rng(31)
+    a = rng.standard_normal((6, 2, 3, 4))
+    b = rng.standard_normal((6, 2, 3, 4))
+    assert math.isclose(o.inner(a, b), float(np.sum(o.to_full(a) * o.to_full(b))), rel_tol=1e-13)
+    assert np.allclose(o.from_full(o.to_full(a)), a)
+    sig = o.stress(prob, a)
+    full = o.to_full(a)
+    for r in range(2):
+        sel = prob.phase == r
+        C4 = o.isotropic_stiffness(prob.lam[r], prob.mu[r])
+        ref = np.einsum("ijkl,kl...->ij...", C4, full[:, :, sel])
+        assert np.allclose(o.to_full(sig)[:, :, sel], ref, rtol=1e-13, atol=1e-13)
+        eng = a[:, sel] * np.array([1, 1, 1, 2, 2, 2])[:, None]
+        assert np.allclose(sig[:, sel], o.voigt_matrix(prob.lam[r], prob.mu[r]) @ eng,
+                           rtol=1e-13, atol=1e-13)
+    tau = o.polarization(prob, a)
+    p0 = o.Problem(phase=prob.phase, lam=prob.lam - prob.lam0, mu=prob.mu - prob.mu0,
+                   lam0=prob.lam0, mu0=prob.mu0)
+    assert np.allclose(tau, o.stress(p0, a), rtol=1e-13, atol=1e-13)
