@@ -658,3 +658,19 @@ def test_tensor_helpers_stress_and_polarization_by_independent_routes():
     p0 = o.Problem(phase=prob.phase, lam=prob.lam - prob.lam0, mu=prob.mu - prob.mu0,
                    lam0=prob.lam0, mu0=prob.mu0)
     assert np.allclose(tau, o.stress(p0, a), rtol=1e-13, atol=1e-13)
+
+
+def test_recentring_reading_preserves_the_map():
+    """The float32 re-centring of the GPU solver (eps = base + y, iterate
+    y -> r + F_u y with r = F(base) - base) is the same affine map written in
+    shifted coordinates: F(base + y) - base = r + F_u y for any base and y, so
+    Z, H and the fixed point are unchanged."""
+    prob = _prob((4, 4, 4), seed=4, c_ratio=(1.0, 30.0))
+    rng = _rng(41)
+    E = np.array([0.2, -0.1, 0.05, 0.03, 0.0, -0.02])
+    base = rng.standard_normal((6, 4, 4, 4))
+    y = rng.standard_normal((6, 4, 4, 4))
+    lhs = o.apply_F(prob, base + y, E) - base
+    r = o.apply_F(prob, base, E) - base
+    rhs = r + o.apply_F_linear(prob, y)
+    assert np.allclose(lhs, rhs, rtol=1e-12, atol=1e-12 * np.max(np.abs(lhs)))
