@@ -674,3 +674,43 @@ def test_recentring_reading_preserves_the_map():
     r = o.apply_F(prob, base, E) - base
     rhs = r + o.apply_F_linear(prob, y)
     assert np.allclose(lhs, rhs, rtol=1e-12, atol=1e-12 * np.max(np.abs(lhs)))
+
+
+# ----------------------------------------------------------------------------
+# The stopping test (fixed-point increment) on a homogeneous cell
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("E_comp,E_val,U_comp,expected_over_a", [
+    (0, 1.0, 5, 1.0),              # E = e1 (x) e1, |E| = 1; u12 = a: |U| = a sqrt 2
+    (3, 0.5, 0, 1.0),              # E = eps23 = 1/2 (gamma23 = 1), |E| = 1/sqrt 2; u11 = a
+    (3, 0.5, 4, math.sqrt(2.0)),   # same E; u13 = a: |U| = a sqrt 2
+    (2, 2.0, 1, 0.25 * math.sqrt(2.0)),   # E = 2 e3 (x) e3, |E| = 2; u22 = a: a / (2 sqrt 2)
+])
+def test_residual_is_frobenius_rms_of_the_increment_over_the_norm_of_E(E_comp, E_val, U_comp,
+                                                                      expected_over_a):
+    """On a homogeneous cell (C = C0) the polarization vanishes, so F(eps) = E
+    for every eps (Section 2, Eq. 2.5).  With eps = E + U cos(2 pi m . x) the
+    increment F(eps) - eps is -U cos(.), and the stopping test of reading 6
+    is its root-mean-square Frobenius norm over the voxels divided by the
+    Frobenius norm of E: sqrt(<cos^2>) |U|_F / |E|_F = |U|_F / (sqrt 2 |E|_F),
+    the mean of cos^2 over the grid being 1/2 for a mode whose double is not
+    a multiple of the grid in every direction.  The expected values are
+    worked out by hand from the full 3x3 tensors (a shear entry appears
+    twice), so a dropped sqrt(n), a missing shear weight or a wrong norm of E
+    changes them."""
+    shape = (4, 6, 8)
+    lam, mu = ms.lame(1.0, 0.3)
+    prob = o.Problem(phase=np.zeros(shape, np.uint8), lam=np.array([lam]), mu=np.array([mu]),
+                     lam0=lam, mu0=mu)
+    E = np.zeros(6)
+    E[E_comp] = E_val
+    nz, ny, nx = shape
+    z, y, x = np.meshgrid((np.arange(nz) + 0.5) / nz, (np.arange(ny) + 0.5) / ny,
+                          (np.arange(nx) + 0.5) / nx, indexing="ij")
+    wave = np.cos(2 * np.pi * (1 * x + 2 * y + 1 * z))
+    a = 0.37
+    eps = o.uniform(E, shape)
+    eps[U_comp] += a * wave
+    xi = o.apply_F(prob, eps, E)
+    assert np.allclose(xi, o.uniform(E, shape), atol=1e-13)
+    got = o.residual(prob, xi, eps, E)
+    assert abs(got - a * expected_over_a) < 1e-12 * a
