@@ -12,11 +12,22 @@
 //   pass C (one block per z-plane and component): inverse FFT along y,
 //       complex-to-real tangling, inverse FFT along x of length nx/2, scale.
 //
+// Two generations of kernels implement the passes.  The fused ones
+// (k_plane_fwd, k_pencil_green, k_plane_inv) serve the common sizes: their
+// first and last register FFT steps read and write global memory directly
+// (pass C takes its plane in one bulk asynchronous copy), the (un)tangling
+// of the half-length x transform is fused into an x step, the real DC and
+// Nyquist x columns travel as one complex column so that the y transforms
+// run on exactly nx/2 columns, and in pass B the forward z step 2, the
+// Green operator and the inverse z step 1 run in registers.  The original
+// kernels (k_pass_a/b/c and the five-pass variant) serve the other sizes.
+//
 // The Green operator of the isotropic reference medium is evaluated on the
 // fly from the unit wave vector n = xi/|xi|:
 //   Gamma0_hat : tau_hat = sym(n (x) w),  w = (v - a n (n.v)) / mu0,
 //   v = tau_hat n,  a = (lam0 + mu0) / (lam0 + 2 mu0),
 // obtained from div(C0 : eps(u) + tau) = 0 in Fourier space.
+#include "async_copy.cuh"
 #include "fft_smem.cuh"
 #include "rpm_internal.h"
 
@@ -342,6 +353,537 @@ __global__ void __launch_bounds__(2 * kThreads, 2) k_pass_b_wide(GridDev g,
   pass_b_body<NZ, TT, 2 * kThreads>(g, spec, mode, ga);
 }
 
+
+// ---------------------------------------------------------------------------
+// Fused-step kernels (square planes nx = ny in {48, 64, 96, 128}; pencils of
+// length nz with 128 / split_n1(nz) pencils per block, nz in {32 .. 128}).
+// ---------------------------------------------------------------------------
+
+// Row task q of an x step over NY rows: (y, n2).  With N2 = 8 the two
+// half-warps take rows y and y + 8, so that the 8-byte accesses of one
+// instruction fall in distinct banks (row stride nx/2 + 1 float2).
+template <int N2, int NY>
+__device__ __forceinline__ void row_task(int q, int& y, int& n2) {
+  if (N2 == 8 && NY % 16 == 0) {
+    n2 = q & 7;
+    const int h = (q >> 3) & 1, g = q >> 4;
+    y = (g & 7) + ((g >> 3) << 4) + (h << 3);
+  } else {
+    n2 = q % N2;
+    y = q / N2;
+  }
+}
+
+// Pass A, one block per (z, component).  x step 1 reads the strain rows from
+// global memory and forms tau on the way in; x step 2 is fused with the
+// real-to-complex untangling; the (real) DC and Nyquist x columns are stored
+// together as X_0 + i X_nx/2 in column 0, so the y transform runs on nx/2
+// columns; y step 2 writes the spectrum plane to global memory, and the
+// packed column is separated last (A_k = (C_k + conj C_-k) / 2,
+// B_k = (C_k - conj C_-k) / 2i).
+// 16-point x steps (nx = 96) need more registers than three blocks per SM allow
+template <int NX, int NY>
+__global__ void __launch_bounds__(kPlaneThreads, Split<NX / 2>::N1 >= 16 ? 2 : kPlaneMinBlocks)
+    k_plane_fwd(GridDev g, const float* __restrict__ in, float2* __restrict__ spec, int mode) {
+  constexpr int NXH = NX / 2, SX = NXH + 1;
+  constexpr int X1 = Split<NXH>::N1, X2 = Split<NXH>::N2;
+  constexpr int Y1 = Split<NY>::N1, Y2 = Split<NY>::N2;
+  static_assert(X2 > 1 && X1 % 2 == 0, "x split must have two steps and an even first factor");
+  extern __shared__ __align__(128) float2 sm[];
+  float2* P = sm;                      // [NY][SX]: the spectrum plane's own layout
+  float2* twx = P + NY * SX;
+  float2* twy = twx + NXH;
+  float2* r2c = twy + NY;
+  float2* dm = r2c + SX;
+  const int c = blockIdx.x, z = blockIdx.y;
+  for (int i = threadIdx.x; i < NXH; i += blockDim.x) twx[i] = g.tw_x[i];
+  for (int i = threadIdx.x; i < NY; i += blockDim.x) twy[i] = g.tw_y[i];
+  for (int i = threadIdx.x; i < SX; i += blockDim.x) r2c[i] = g.r2c_w[i];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) dm[i] = g.dmat[i];
+  __syncthreads();
+  const size_t nf2 = (size_t)g.n / 2;
+  const float2* in2 = reinterpret_cast<const float2*>(in) + (size_t)z * NY * NXH;
+  const uchar2* ph2 = reinterpret_cast<const uchar2*>(g.phase) + (size_t)z * NY * NXH;
+  const bool three = mode != GM_RAW_TAU && c < 3;
+  for (int q = threadIdx.x; q < NY * X2; q += blockDim.x) {
+    int y, n2;
+    row_task<X2, NY>(q, y, n2);
+    const int rb = y * NXH + n2;
+    float2 v[X1];
+    if (!three) {
+      float2 a[X1];
+      uchar2 ph[X1];
+#pragma unroll
+      for (int i = 0; i < X1; ++i) {
+        a[i] = in2[c * nf2 + rb + X2 * i];
+        if (mode != GM_RAW_TAU) ph[i] = ph2[rb + X2 * i];
+      }
+#pragma unroll
+      for (int i = 0; i < X1; ++i) {
+        if (mode == GM_RAW_TAU) {
+          v[i] = a[i];
+        } else {
+          const float2 d0 = dm[ph[i].x], d1 = dm[ph[i].y];
+          v[i] = make_float2(2.f * d0.y * a[i].x, 2.f * d1.y * a[i].y);
+        }
+      }
+    } else {
+      constexpr int H = X1 >= 4 ? 4 : X1;   // voxel pairs loaded per batch
+#pragma unroll
+      for (int i0 = 0; i0 < X1; i0 += H) {
+        float2 a[H], b[H], d[H];
+        uchar2 ph[H];
+#pragma unroll
+        for (int j = 0; j < H; ++j) {
+          const int i = i0 + j;
+          a[j] = in2[rb + X2 * i];
+          b[j] = in2[nf2 + rb + X2 * i];
+          d[j] = in2[2 * nf2 + rb + X2 * i];
+          ph[j] = ph2[rb + X2 * i];
+        }
+#pragma unroll
+        for (int j = 0; j < H; ++j) {
+          const float2 d0 = dm[ph[j].x], d1 = dm[ph[j].y];
+          const float2 e = c == 0 ? a[j] : (c == 1 ? b[j] : d[j]);
+          v[i0 + j] = make_float2(fmaf(d0.x, a[j].x + b[j].x + d[j].x, 2.f * d0.y * e.x),
+                                  fmaf(d1.x, a[j].y + b[j].y + d[j].y, 2.f * d1.y * e.y));
+        }
+      }
+    }
+    RegDft<X1, false>::run(v);
+#pragma unroll
+    for (int k1 = 1; k1 < X1; ++k1) v[k1] = cmul(v[k1], twx[n2 * X1 + k1]);
+    float2* p = P + y * SX + n2;
+#pragma unroll
+    for (int i = 0; i < X1; ++i) p[i * X2] = v[i];
+  }
+  __syncthreads();
+  // x step 2 fused with the untangling.  Slot group k1 holds the
+  // frequencies k1 + X1 i; the partner nx/2 - k of k lies in group X1 - k1
+  // (groups 0 and X1/2 pair with themselves).
+  constexpr int NU = X1 / 2 + 1;
+  for (int t = threadIdx.x; t < NY * NU; t += blockDim.x) {
+    const int b = t % NY, u = t / NY;
+    float2* p = P + b * SX;
+    if (u == 0 || u == X1 / 2) {
+      const int k1 = u;
+      float2 v[X2];
+#pragma unroll
+      for (int i = 0; i < X2; ++i) v[i] = p[k1 * X2 + i];
+      RegDft<X2, false>::run(v);
+      float2 o[X2];
+      if (k1 == 0) {
+        const float2 z0 = v[0];
+        o[0] = make_float2(z0.x + z0.y, z0.x - z0.y);   // (X_0, X_nx/2), both real
+#pragma unroll
+        for (int i = 1; i < X2; ++i) {
+          const int ip = X2 - i;
+          if (i < ip) {
+            o[i] = r2c_post(v[i], v[ip], r2c[X1 * i]);
+            o[ip] = r2c_post(v[ip], v[i], r2c[X1 * ip]);
+          } else if (i == ip) {
+            o[i] = r2c_post(v[i], v[i], r2c[X1 * i]);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < X2; ++i) {
+          const int ip = X2 - 1 - i;
+          if (i < ip) {
+            o[i] = r2c_post(v[i], v[ip], r2c[X1 / 2 + X1 * i]);
+            o[ip] = r2c_post(v[ip], v[i], r2c[X1 / 2 + X1 * ip]);
+          } else if (i == ip) {
+            o[i] = r2c_post(v[i], v[i], r2c[X1 / 2 + X1 * i]);
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < X2; ++i) p[k1 * X2 + i] = o[i];
+    } else {
+      const int k1 = u, k1p = X1 - u;
+      float2 va[X2], vb[X2];
+#pragma unroll
+      for (int i = 0; i < X2; ++i) {
+        va[i] = p[k1 * X2 + i];
+        vb[i] = p[k1p * X2 + i];
+      }
+      RegDft<X2, false>::run(va);
+      RegDft<X2, false>::run(vb);
+      float2 oa[X2], ob[X2];
+#pragma unroll
+      for (int i = 0; i < X2; ++i) {
+        const int ip = X2 - 1 - i;
+        oa[i] = r2c_post(va[i], vb[ip], r2c[k1 + X1 * i]);
+        ob[ip] = r2c_post(vb[ip], va[i], r2c[k1p + X1 * ip]);
+      }
+#pragma unroll
+      for (int i = 0; i < X2; ++i) {
+        p[k1 * X2 + i] = oa[i];
+        p[k1p * X2 + i] = ob[i];
+      }
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < NXH * Y2; t += blockDim.x) {   // y step 1
+    const int b = t % NXH, n2 = t / NXH;
+    float2* p = P + b + n2 * SX;
+    float2 v[Y1];
+#pragma unroll
+    for (int i = 0; i < Y1; ++i) v[i] = p[i * Y2 * SX];
+    RegDft<Y1, false>::run(v);
+#pragma unroll
+    for (int k1 = 1; k1 < Y1; ++k1) v[k1] = cmul(v[k1], twy[n2 * Y1 + k1]);
+#pragma unroll
+    for (int i = 0; i < Y1; ++i) p[i * Y2 * SX] = v[i];
+  }
+  __syncthreads();
+  float2* out = spec + ((size_t)c * g.nz + z) * g.plane;
+  for (int t = threadIdx.x; t < NXH * Y1; t += blockDim.x) {   // y step 2 -> global
+    const int b = t % NXH, k1 = t / NXH;
+    float2* p = P + b + k1 * Y2 * SX;
+    float2 v[Y2];
+#pragma unroll
+    for (int i = 0; i < Y2; ++i) v[i] = p[i * SX];
+    RegDft<Y2, false>::run(v);
+    if (b == 0) {
+#pragma unroll
+      for (int i = 0; i < Y2; ++i) p[i * SX] = v[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < Y2; ++i) out[(size_t)(k1 * Y2 + i) * SX + b] = v[i];
+    }
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < NY; s += blockDim.x) {   // separate the packed column
+    const int k = freq_of<NY>(s);
+    const int sn = slot_of<NY>((NY - k) % NY);
+    const float2 a = P[s * SX], b = P[sn * SX];
+    out[(size_t)s * SX] = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+    out[(size_t)s * SX + NXH] = make_float2(0.5f * (a.y + b.y), -0.5f * (a.x - b.x));
+  }
+}
+
+// Pass C, one block per (component, z).  The spectrum plane arrives by one
+// bulk asynchronous copy; y step 1 packs the DC and Nyquist x columns as
+// X_0 + i X_nx/2 (their inverse y transforms are real, so the result holds
+// both in its real and imaginary parts); the tangling is fused into x step
+// 1; x step 2 writes the real rows to global memory, scaled.
+template <int NX, int NY>
+__global__ void __launch_bounds__(kPlaneThreads, kPlaneMinBlocks)
+    k_plane_inv(GridDev g, const float2* __restrict__ spec, float* __restrict__ outp,
+                float scale) {
+  constexpr int NXH = NX / 2, SX = NXH + 1, PL = NY * SX;
+  constexpr int X1 = Split<NXH>::N1, X2 = Split<NXH>::N2;
+  constexpr int Y1 = Split<NY>::N1, Y2 = Split<NY>::N2;
+  static_assert(X2 > 1 && X1 % 2 == 0, "x split must have two steps and an even first factor");
+  static_assert((PL * 8) % 16 == 0, "bulk copy size");
+  extern __shared__ __align__(128) float2 sm[];
+  float2* P = sm;
+  float2* twx = P + PL;
+  float2* twy = twx + NXH;
+  float2* r2c = twy + NY;
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int fail;
+  const int item = blockIdx.x;   // c * nz + z
+  if (threadIdx.x == 0) {
+    fail = 0;
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+    mbar_arrive_expect_tx(&bar, PL * 8);
+    bulk_load(P, spec + (size_t)item * g.plane, PL * 8, &bar);
+  }
+  for (int i = threadIdx.x; i < NXH; i += blockDim.x) twx[i] = g.tw_x[i];
+  for (int i = threadIdx.x; i < NY; i += blockDim.x) twy[i] = g.tw_y[i];
+  for (int i = threadIdx.x; i < SX; i += blockDim.x) r2c[i] = g.r2c_w[i];
+  __syncthreads();
+  if (!mbar_wait(&bar, 0)) fail = 1;
+  __syncthreads();
+  if (fail) {   // the copy never completed: record it and leave the plane alone
+    if (threadIdx.x == 0) {
+      atomicExch(g.err, 1);
+      mbar_wait(&bar, 0);
+    }
+    return;
+  }
+  for (int t = threadIdx.x; t < NXH * Y1; t += blockDim.x) {   // y step 1 (inverse)
+    const int b = t % NXH, k1 = t / NXH;
+    float2* p = P + k1 * Y2 * SX + b;
+    float2 v[Y2];
+#pragma unroll
+    for (int i = 0; i < Y2; ++i) v[i] = p[i * SX];
+    if (b == 0) {
+#pragma unroll
+      for (int i = 0; i < Y2; ++i) {
+        const float2 w = p[i * SX + NXH];
+        v[i] = make_float2(v[i].x - w.y, v[i].y + w.x);
+      }
+    }
+    RegDft<Y2, true>::run(v);
+#pragma unroll
+    for (int n2 = 1; n2 < Y2; ++n2) v[n2] = cmulc(v[n2], twy[n2 * Y1 + k1]);
+#pragma unroll
+    for (int i = 0; i < Y2; ++i) p[i * SX] = v[i];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < NXH * Y2; t += blockDim.x) {   // y step 2 (inverse)
+    const int b = t % NXH, n2 = t / NXH;
+    float2* p = P + b + n2 * SX;
+    float2 v[Y1];
+#pragma unroll
+    for (int i = 0; i < Y1; ++i) v[i] = p[i * Y2 * SX];
+    RegDft<Y1, true>::run(v);
+#pragma unroll
+    for (int i = 0; i < Y1; ++i) p[i * Y2 * SX] = v[i];
+  }
+  __syncthreads();
+  constexpr int NU = X1 / 2 + 1;   // tangling fused into x step 1 (inverse)
+  for (int t = threadIdx.x; t < NY * NU; t += blockDim.x) {
+    const int b = t % NY, u = t / NY;
+    float2* p = P + b * SX;
+    if (u == 0 || u == X1 / 2) {
+      const int k1 = u;
+      float2 v[X2];
+#pragma unroll
+      for (int i = 0; i < X2; ++i) v[i] = p[k1 * X2 + i];
+      float2 o[X2];
+      if (k1 == 0) {
+        o[0] = make_float2(v[0].x + v[0].y, v[0].x - v[0].y);   // from (x_DC, x_Nyquist)
+#pragma unroll
+        for (int i = 1; i < X2; ++i) {
+          const int ip = X2 - i;
+          if (i < ip) {
+            o[i] = c2r_pre(v[i], v[ip], r2c[X1 * i]);
+            o[ip] = c2r_pre(v[ip], v[i], r2c[X1 * ip]);
+          } else if (i == ip) {
+            o[i] = c2r_pre(v[i], v[i], r2c[X1 * i]);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < X2; ++i) {
+          const int ip = X2 - 1 - i;
+          if (i < ip) {
+            o[i] = c2r_pre(v[i], v[ip], r2c[X1 / 2 + X1 * i]);
+            o[ip] = c2r_pre(v[ip], v[i], r2c[X1 / 2 + X1 * ip]);
+          } else if (i == ip) {
+            o[i] = c2r_pre(v[i], v[i], r2c[X1 / 2 + X1 * i]);
+          }
+        }
+      }
+      RegDft<X2, true>::run(o);
+#pragma unroll
+      for (int n2 = 1; n2 < X2; ++n2) o[n2] = cmulc(o[n2], twx[n2 * X1 + k1]);
+#pragma unroll
+      for (int i = 0; i < X2; ++i) p[k1 * X2 + i] = o[i];
+    } else {
+      const int k1 = u, k1p = X1 - u;
+      float2 va[X2], vb[X2];
+#pragma unroll
+      for (int i = 0; i < X2; ++i) {
+        va[i] = p[k1 * X2 + i];
+        vb[i] = p[k1p * X2 + i];
+      }
+      float2 oa[X2], ob[X2];
+#pragma unroll
+      for (int i = 0; i < X2; ++i) {
+        const int ip = X2 - 1 - i;
+        oa[i] = c2r_pre(va[i], vb[ip], r2c[k1 + X1 * i]);
+        ob[ip] = c2r_pre(vb[ip], va[i], r2c[k1p + X1 * ip]);
+      }
+      RegDft<X2, true>::run(oa);
+      RegDft<X2, true>::run(ob);
+#pragma unroll
+      for (int n2 = 1; n2 < X2; ++n2) {
+        oa[n2] = cmulc(oa[n2], twx[n2 * X1 + k1]);
+        ob[n2] = cmulc(ob[n2], twx[n2 * X1 + k1p]);
+      }
+#pragma unroll
+      for (int i = 0; i < X2; ++i) {
+        p[k1 * X2 + i] = oa[i];
+        p[k1p * X2 + i] = ob[i];
+      }
+    }
+  }
+  __syncthreads();
+  const int c = item / g.nz, z = item - c * g.nz;
+  float2* out2 = reinterpret_cast<float2*>(outp) + (size_t)c * (g.n / 2) + (size_t)z * NY * NXH;
+  for (int q = threadIdx.x; q < NY * X2; q += blockDim.x) {   // x step 2 (inverse) -> global
+    int y, n2;
+    row_task<X2, NY>(q, y, n2);
+    const float2* p = P + y * SX + n2;
+    float2 v[X1];
+#pragma unroll
+    for (int i = 0; i < X1; ++i) v[i] = p[i * X2];
+    RegDft<X1, true>::run(v);
+    float2* o = out2 + y * NXH + n2;
+#pragma unroll
+    for (int i = 0; i < X1; ++i) o[i * X2] = cscale(v[i], scale);
+  }
+}
+
+// Pass B with T = 128 / split_n1(nz) pencils per block and 256 threads.
+// Forward z step 1 reads the spectrum from global memory; forward step 2, the
+// Green operator and inverse step 1 run in registers on one (pencil, k1)
+// group per pair of threads, lanes l and l + 16 holding the normal and the
+// shear components of the same frequencies and exchanging their partial sums
+// of tau_hat n with one shuffle per value; inverse step 2 writes back to
+// global memory.
+template <int NZ>
+struct PencilFused {
+  static constexpr int Z1 = Split<NZ>::N1, Z2 = Split<NZ>::N2;
+  static constexpr int T = 128 / Z1;
+  static constexpr int NZP = NZ + 1;
+};
+
+template <int NZ>
+__global__ void __launch_bounds__(kThreads, 3) k_pencil_green(GridDev g, float2* __restrict__ spec,
+                                                             int mode, GammaArgs ga) {
+  using C = PencilFused<NZ>;
+  constexpr int Z1 = C::Z1, Z2 = C::Z2, T = C::T, NZP = C::NZP;
+  static_assert(T * Z1 * 2 == kThreads, "one thread pair per (pencil, k1) group");
+  extern __shared__ __align__(128) float2 sm[];
+  float2* B = sm;                       // [6][T][NZP]
+  float2* twz = B + 6 * T * NZP;
+  __shared__ float4 pen[T];             // per pencil: (xi_x, xi_y, has-Nyquist, non-zero count)
+  const int m0 = blockIdx.x * T;
+  const int plane = g.plane;
+  for (int i = threadIdx.x; i < NZ; i += blockDim.x) twz[i] = g.tw_z[i];
+  if (threadIdx.x < T) {
+    const int m = m0 + threadIdx.x;
+    float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (m < plane) {
+      const int sxn = g.nxh + 1;
+      const int sy = m / sxn, sx = m - sy * sxn;
+      const int2 fx = g.fx[sx], fy = g.fy[sy];
+      q = make_float4(fx.x * g.inv_lx, fy.x * g.inv_ly, (float)(fx.y | fy.y),
+                      (float)((fx.x != 0) + (fy.x != 0)));
+    }
+    pen[threadIdx.x] = q;
+  }
+  __syncthreads();
+  // forward step 1; task q -> (pencil t fastest, then component, then n2):
+  // a half-warp covers two components, whose lines are 16 words apart in banks
+  for (int q = threadIdx.x; q < 6 * T * Z2; q += blockDim.x) {
+    const int t = q % T, c = (q / T) % 6, n2 = q / (6 * T);
+    const int m = m0 + t;
+    const float2* src = spec + ((size_t)c * NZ + n2) * plane + m;
+    const size_t zs = (size_t)Z2 * plane;
+    float2 v[Z1];
+#pragma unroll
+    for (int i = 0; i < Z1; ++i) v[i] = m < plane ? src[i * zs] : make_float2(0.f, 0.f);
+    RegDft<Z1, false>::run(v);
+#pragma unroll
+    for (int k1 = 1; k1 < Z1; ++k1) v[k1] = cmul(v[k1], twz[n2 * Z1 + k1]);
+    float2* p = B + (c * T + t) * NZP + n2;
+#pragma unroll
+    for (int i = 0; i < Z1; ++i) p[i * Z2] = v[i];
+  }
+  __syncthreads();
+  {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int pi = w * 16 + (lane & 15);
+    const int h = lane >> 4;             // 0: tau11 tau22 tau33, 1: tau23 tau13 tau12
+    const int t = pi % T, k1 = pi / T;
+    float2 v[3][Z2];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float2* p = B + ((3 * h + j) * T + t) * NZP + k1 * Z2;
+#pragma unroll
+      for (int i = 0; i < Z2; ++i) v[j][i] = p[i];
+      RegDft<Z2, false>::run(v[j]);
+    }
+    const float4 q = pen[t];
+#pragma unroll
+    for (int k2 = 0; k2 < Z2; ++k2) {
+      const int kz = k1 + Z1 * k2;
+      const int mz = (2 * kz < NZ) ? kz : kz - NZ;
+      const bool nyqz = (NZ % 2 == 0) && (2 * kz == NZ);
+      const int nnz = (int)q.w + (mz != 0);
+      const bool zero_f = nnz == 0;
+      const bool masked = !zero_f && g.nyquist == 0 && nnz >= 2 && (q.z != 0.f || nyqz);
+      float n1 = 0.f, n2 = 0.f, n3 = 0.f;
+      if (!zero_f) {
+        const float x1 = q.x, x2 = q.y, x3 = mz * g.inv_lz;
+        const float inv = 1.f / sqrtf(x1 * x1 + x2 * x2 + x3 * x3);
+        n1 = x1 * inv;
+        n2 = x2 * inv;
+        n3 = x3 * inv;
+      }
+      const float2 a0 = v[0][k2], a1 = v[1][k2], a2 = v[2][k2];
+      float2 p1, p2, p3;   // this half's share of v = tau_hat n
+      if (h == 0) {
+        p1 = make_float2(a0.x * n1, a0.y * n1);
+        p2 = make_float2(a1.x * n2, a1.y * n2);
+        p3 = make_float2(a2.x * n3, a2.y * n3);
+      } else {
+        p1 = make_float2(a2.x * n2 + a1.x * n3, a2.y * n2 + a1.y * n3);
+        p2 = make_float2(a2.x * n1 + a0.x * n3, a2.y * n1 + a0.y * n3);
+        p3 = make_float2(a1.x * n1 + a0.x * n2, a1.y * n1 + a0.y * n2);
+      }
+      p1.x += __shfl_xor_sync(0xffffffffu, p1.x, 16);
+      p1.y += __shfl_xor_sync(0xffffffffu, p1.y, 16);
+      p2.x += __shfl_xor_sync(0xffffffffu, p2.x, 16);
+      p2.y += __shfl_xor_sync(0xffffffffu, p2.y, 16);
+      p3.x += __shfl_xor_sync(0xffffffffu, p3.x, 16);
+      p3.y += __shfl_xor_sync(0xffffffffu, p3.y, 16);
+      const float sx = n1 * p1.x + n2 * p2.x + n3 * p3.x;
+      const float sy = n1 * p1.y + n2 * p2.y + n3 * p3.y;
+      const float2 w1 = make_float2((p1.x - ga.a * n1 * sx) * ga.inv_mu0,
+                                    (p1.y - ga.a * n1 * sy) * ga.inv_mu0);
+      const float2 w2 = make_float2((p2.x - ga.a * n2 * sx) * ga.inv_mu0,
+                                    (p2.y - ga.a * n2 * sy) * ga.inv_mu0);
+      const float2 w3 = make_float2((p3.x - ga.a * n3 * sx) * ga.inv_mu0,
+                                    (p3.y - ga.a * n3 * sy) * ga.inv_mu0);
+      float2 o0, o1, o2;
+      if (h == 0) {
+        o0 = make_float2(-n1 * w1.x, -n1 * w1.y);
+        o1 = make_float2(-n2 * w2.x, -n2 * w2.y);
+        o2 = make_float2(-n3 * w3.x, -n3 * w3.y);
+      } else {
+        o0 = make_float2(-0.5f * (n2 * w3.x + n3 * w2.x), -0.5f * (n2 * w3.y + n3 * w2.y));
+        o1 = make_float2(-0.5f * (n1 * w3.x + n3 * w1.x), -0.5f * (n1 * w3.y + n3 * w1.y));
+        o2 = make_float2(-0.5f * (n1 * w2.x + n2 * w1.x), -0.5f * (n1 * w2.y + n2 * w1.y));
+      }
+      if (zero_f) {
+        const bool full = mode == GM_FULL_MAP;
+        o0 = make_float2(full ? ga.En[3 * h] : 0.f, 0.f);
+        o1 = make_float2(full ? ga.En[3 * h + 1] : 0.f, 0.f);
+        o2 = make_float2(full ? ga.En[3 * h + 2] : 0.f, 0.f);
+      } else if (masked) {
+        o0 = o1 = o2 = make_float2(0.f, 0.f);
+      }
+      v[0][k2] = o0;
+      v[1][k2] = o1;
+      v[2][k2] = o2;
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      RegDft<Z2, true>::run(v[j]);
+#pragma unroll
+      for (int n2 = 1; n2 < Z2; ++n2) v[j][n2] = cmulc(v[j][n2], twz[n2 * Z1 + k1]);
+      float2* p = B + ((3 * h + j) * T + t) * NZP + k1 * Z2;
+#pragma unroll
+      for (int i = 0; i < Z2; ++i) p[i] = v[j][i];
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < 6 * T * Z2; q += blockDim.x) {   // inverse step 2 -> global
+    const int t = q % T, c = (q / T) % 6, n2 = q / (6 * T);
+    const int m = m0 + t;
+    const float2* p = B + (c * T + t) * NZP + n2;
+    float2 v[Z1];
+#pragma unroll
+    for (int i = 0; i < Z1; ++i) v[i] = p[i * Z2];
+    RegDft<Z1, true>::run(v);
+    if (m < plane) {
+      float2* dst = spec + ((size_t)c * NZ + n2) * plane + m;
+      const size_t zs = (size_t)Z2 * plane;
+#pragma unroll
+      for (int i = 0; i < Z1; ++i) dst[i * zs] = v[i];
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Five-pass variant for planes that do not fit in shared memory (nx = 256)
 // and for nx != ny: rows along x, pencils along y, the z pass above, pencils
@@ -616,6 +1158,85 @@ static cudaError_t launch_ypencil(const GridDev& g, float2* spec, bool inv, cuda
   return cudaGetLastError();
 }
 
+
+// the fused plane passes: nx = ny with a two-step x split of nx/2 and an even
+// first factor; the fused pencil pass: 128 / split_n1(nz) pencils per block
+#define RPM_FUSED_PLANE_SIZES(X) X(48) X(64) X(96) X(128)
+#define RPM_FUSED_Z_SIZES(X) X(32) X(48) X(64) X(96) X(128)
+
+template <int NX>
+static cudaError_t launch_fused_plane(const GridDev& g, const float* in, float* out, float2* spec,
+                                      int mode, int which, cudaStream_t st) {
+  constexpr int NXH = NX / 2, SX = NXH + 1;
+  const size_t tab = (size_t)(NXH + NX + SX) * sizeof(float2);
+  const size_t smem = (size_t)NX * SX * sizeof(float2) + tab;
+  cudaError_t e;
+  if (which == 0) {
+    if ((e = set_smem(k_plane_fwd<NX, NX>, smem + 256 * sizeof(float2))) != cudaSuccess) return e;
+    k_plane_fwd<NX, NX><<<dim3(6, g.nz), kPlaneThreads, smem + 256 * sizeof(float2), st>>>(
+        g, in, spec, mode);
+  } else {
+    if ((e = set_smem(k_plane_inv<NX, NX>, smem)) != cudaSuccess) return e;
+    k_plane_inv<NX, NX><<<6 * g.nz, kPlaneThreads, smem, st>>>(g, spec, out,
+                                                               1.0f / (float)g.n);
+  }
+  return cudaGetLastError();
+}
+
+template <int NZ>
+static cudaError_t launch_fused_pencil(const GridDev& g, float2* spec, int mode,
+                                       const GammaArgs& ga, cudaStream_t st) {
+  using C = PencilFused<NZ>;
+  const size_t smem = (size_t)(6 * C::T * C::NZP + NZ) * sizeof(float2);
+  cudaError_t e;
+  if ((e = set_smem(k_pencil_green<NZ>, smem)) != cudaSuccess) return e;
+  k_pencil_green<NZ><<<(g.plane + C::T - 1) / C::T, kThreads, smem, st>>>(g, spec, mode, ga);
+  return cudaGetLastError();
+}
+
+static bool fused_plane_ok(const GridDev& g, const float2* spec) {
+  if (g.nx != g.ny || ((uintptr_t)spec & 15) != 0) return false;
+  switch (g.nx) {
+#define RPM_CASE(N) case N:
+    RPM_FUSED_PLANE_SIZES(RPM_CASE)
+#undef RPM_CASE
+    return true;
+    default: return false;
+  }
+}
+
+static bool fused_pencil_ok(int nz) {
+  switch (nz) {
+#define RPM_CASE(N) case N:
+    RPM_FUSED_Z_SIZES(RPM_CASE)
+#undef RPM_CASE
+    return true;
+    default: return false;
+  }
+}
+
+static cudaError_t dispatch_fused_plane(const GridDev& g, const float* in, float* out,
+                                        float2* spec, int mode, int which, cudaStream_t st) {
+  switch (g.nx) {
+#define RPM_CASE(N) \
+  case N: return launch_fused_plane<N>(g, in, out, spec, mode, which, st);
+    RPM_FUSED_PLANE_SIZES(RPM_CASE)
+#undef RPM_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+static cudaError_t dispatch_fused_pencil(const GridDev& g, float2* spec, int mode,
+                                         const GammaArgs& ga, cudaStream_t st) {
+  switch (g.nz) {
+#define RPM_CASE(N) \
+  case N: return launch_fused_pencil<N>(g, spec, mode, ga, st);
+    RPM_FUSED_Z_SIZES(RPM_CASE)
+#undef RPM_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 #define RPM_SIZES(X) X(4) X(6) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(256)
 #define RPM_Z_SIZES(X) \
   X(1) X(2) X(3) X(4) X(6) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(256)
@@ -691,6 +1312,7 @@ static cudaError_t dispatch_pencil(const GridDev& g, float2* spec, int mode, con
 int gamma_launches(int nx, int ny) { return plane_fits(nx, ny) ? 3 : 5; }
 
 int pencil_tile(const GridDev& g) {
+  if (fused_pencil_ok(g.nz)) return 128 / split_n1(g.nz);
   int t0;
   switch (g.nz) {
 #define RPM_CASE(N) \
@@ -715,14 +1337,23 @@ cudaError_t launch_apply_gamma(const GridDev& g, const float* in, float* out, fl
   ga.a = (float)((l0 + m0) / (l0 + 2.0 * m0));
   ga.inv_mu0 = (float)(1.0 / m0);
   cudaError_t e;
+  const bool zf = fused_pencil_ok(g.nz);
+  auto zpass = [&]() {
+    return zf ? dispatch_fused_pencil(g, spec, mode, ga, st) : dispatch_pencil(g, spec, mode, ga, st);
+  };
+  if (fused_plane_ok(g, spec)) {
+    if ((e = dispatch_fused_plane(g, in, out, spec, mode, 0, st)) != cudaSuccess) return e;
+    if ((e = zpass()) != cudaSuccess) return e;
+    return dispatch_fused_plane(g, in, out, spec, mode, 1, st);
+  }
   if (plane_fits(g.nx, g.ny)) {
     if ((e = dispatch_plane(g, in, out, spec, mode, 0, st)) != cudaSuccess) return e;
-    if ((e = dispatch_pencil(g, spec, mode, ga, st)) != cudaSuccess) return e;
+    if ((e = zpass()) != cudaSuccess) return e;
     return dispatch_plane(g, in, out, spec, mode, 1, st);
   }
   if ((e = dispatch_rows(g, in, out, spec, mode, 0, st)) != cudaSuccess) return e;
   if ((e = dispatch_ypencil(g, spec, false, st)) != cudaSuccess) return e;
-  if ((e = dispatch_pencil(g, spec, mode, ga, st)) != cudaSuccess) return e;
+  if ((e = zpass()) != cudaSuccess) return e;
   if ((e = dispatch_ypencil(g, spec, true, st)) != cudaSuccess) return e;
   return dispatch_rows(g, in, out, spec, mode, 1, st);
 }

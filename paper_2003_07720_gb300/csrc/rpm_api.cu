@@ -519,6 +519,7 @@ rpm_status rpm_create(const rpm_grid* grid, const uint8_t* phase, int phase_on_d
   const size_t o_db = off; off = align_up(off + 256 * 8, 256);
   const size_t o_pt = off; off = align_up(off + 256 * 16, 256);
   const size_t o_dp = off; off = align_up(off + 256 * 8, 256);
+  const size_t o_err = off; off = align_up(off + 16, 256);
   const size_t tab_bytes = off;
   c->nblk = std::max(dots_blocks_for(c->n), stress_blocks_for(c->n));
   const size_t fbytes = c->fst * sizeof(float);
@@ -572,6 +573,7 @@ rpm_status rpm_create(const rpm_grid* grid, const uint8_t* phase, int phase_on_d
       put(o_dm, dm256.data(), 256 * 8) != cudaSuccess ||
       put(o_cm, cm256.data(), 256 * 8) != cudaSuccess ||
       cudaMemsetAsync(c->dsmall, 0, (kSmall + 1) * 8, c->st) != cudaSuccess ||
+      cudaMemsetAsync(t + o_err, 0, 16, c->st) != cudaSuccess ||
       cudaStreamSynchronize(c->st) != cudaSuccess) {
     rpm_destroy(c);
     return RPM_ERR_CUDA;
@@ -585,6 +587,7 @@ rpm_status rpm_create(const rpm_grid* grid, const uint8_t* phase, int phase_on_d
   g.dmat = (const float2*)(t + o_dm);
   g.cmat = (const float2*)(t + o_cm);
   g.phase = c->phase;
+  g.err = (int*)(t + o_err);
   c->dmat_b = (float2*)(t + o_db);
   c->post = (float4*)(t + o_pt);
   c->dmat_p = (float2*)(t + o_dp);
@@ -929,7 +932,20 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
       return RPM_ERR_CUDA;
   }
   if (!ck(c, cudaEventRecord(c->ev1, c->st), "event")) return RPM_ERR_CUDA;
+  int kerr = 0;
+  if (!ck(c, cudaMemcpyAsync(&kerr, c->g.err, sizeof(int), cudaMemcpyDeviceToHost, c->st),
+          "error flag"))
+    return RPM_ERR_CUDA;
   if (!ops.read_small(kSums, 6)) return RPM_ERR_CUDA;
+  if (kerr) {
+    c->err = "a kernel's bounded wait for an asynchronous copy gave up";
+    cudaMemsetAsync(c->g.err, 0, sizeof(int), c->st);
+    if (info) {
+      inf.status = RPM_ERR_TIMEOUT;
+      *info = inf;
+    }
+    return RPM_ERR_TIMEOUT;
+  }
   for (int k = 0; k < 6; ++k) inf.mean_stress[k] = hs[kSums + k] / (double)c->n;
   float ms = 0;
   cudaEventElapsedTime(&ms, c->ev0, c->ev1);

@@ -18,7 +18,7 @@ enum GammaMode {
 
 // Device-side description of one grid, its FFT tables and the materials.
 struct GridDev {
-  int nx, ny, nz;        // nx == ny, powers of two
+  int nx, ny, nz;        // each 2^a 3^b
   int nxh;               // nx / 2
   long long n;           // voxels
   int plane;             // ny * (nxh + 1): half-spectrum slots per z-plane
@@ -37,6 +37,7 @@ struct GridDev {
   float inv_lx, inv_ly, inv_lz;   // 1 / L_j (frequency scaling)
   int nyquist;           // 0: zero mixed Nyquist frequencies, 1: signed
   int pencil_t;          // pass-B tile variant: 0 default, 1 half, 2 twice the pencils
+  int* err;              // device flag set to 1 when a bounded wait of a kernel gave up
 };
 
 // One Gamma0 application: in [6][n] -> out [6][n] through the spectrum

@@ -53,7 +53,11 @@ def _run(cell, mode, nyq=0, seed=1, E=None):
                                    (1, 8, 256), (32, 64, 32),
                                    # radix-3 lengths (2^a 3^b)
                                    (48, 48, 48), (96, 96, 96), (12, 24, 24), (6, 12, 12),
-                                   (3, 48, 48), (24, 6, 6), (16, 96, 48), (8, 96, 256)])
+                                   (3, 48, 48), (24, 6, 6), (16, 96, 48), (8, 96, 256),
+                                   # fused plane and pencil kernels (square planes 48-128,
+                                   # nz 32-128), alone and with the original ones
+                                   (128, 64, 64), (64, 96, 96), (32, 128, 128), (48, 64, 64),
+                                   (128, 48, 48), (96, 32, 64), (64, 128, 128), (6, 96, 96)])
 @pytest.mark.parametrize("mode", [0, 1, 2])
 def test_apply_gamma_matches_oracle(shape, mode):
     got, ref = _run(_cell(shape, 3), mode)
@@ -89,3 +93,27 @@ def test_gamma_projector_identity_on_gpu():
         torch.cuda.synchronize()
     err = (torch.linalg.vector_norm(g2 + g1) / torch.linalg.vector_norm(g1)).item()
     assert err < 1e-5
+
+
+def test_apply_gamma_full_size_256_ellipsoids():
+    """The 256^3 high-contrast cell (random ellipsoids, 30 % volume fraction,
+    contrast 1e4, C0 = arithmetic mean): one full map F on a random field,
+    every element against the FP64 oracle's map, in the launch configuration
+    the solver uses at this size."""
+    from paper_2003_07720_gb300 import rpm
+    cell = ms.cell_ellipsoids(256, 0, contrast=1e4)
+    E = np.array([0.3, -0.2, 0.1, 0.05, -0.04, 0.07])
+    x = _rng(11).standard_normal((6,) + cell.shape).astype(np.float32)
+    xd = torch.from_numpy(x).cuda()
+    out = torch.full_like(xd, float("nan"))
+    with rpm.Context(cell, rpm.rpm_default_options(p_max=0)) as ctx:
+        ctx.apply_gamma(xd, E, out, rpm.RPM_GAMMA_FULL_MAP)
+        torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    del xd, out
+    ref = o.apply_F(o.Problem.from_cell(cell), x.astype(np.float64), E)
+    assert np.all(np.isfinite(got))
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err < TOL, err
+    # element by element: no voxel off by more than 1e-5 of the field's scale
+    assert np.max(np.abs(got - ref)) < TOL * np.max(np.abs(ref)), np.max(np.abs(got - ref))
