@@ -187,20 +187,24 @@ rpm_status rpm_apply_gamma(rpm_ctx* ctx, const float* in, const double E[6], flo
  * flags, but its scratch (the half spectrum and the FFT/frequency/material
  * tables) is a set of fixed-size file-scope device arrays that every GPU
  * loading the library holds until the process exits (about 6.6 MB).
- *   grid     nx == ny <= 64 and nz <= 64 (and supported as above);
- *            larger grids return RPM_ERR_UNSUPPORTED_GRID.
+ *   grid     nx == ny <= 64 and nz <= 64 (and supported as above); other
+ *            grids return RPM_ERR_UNSUPPORTED_GRID.
  *   phase    DEVICE pointer, uint8 [nz][ny][nx], ids < n_phases.
  *   phases   host array of n_phases (1..256) moduli; c0 the reference medium.
  *   in, out  device fields [6][n] (may not alias); E host double[6]
  *            (required for RPM_GAMMA_FULL_MAP); flags RPM_GAMMA_FULL_MAP,
  *            RPM_GAMMA_LINEAR or RPM_GAMMA_RAW_TAU (RPM_GAMMA_PROJECT needs a context).
  *   cuda_stream  stream for the copies and kernels (NULL: legacy stream).
- * The first call on a device looks up the arrays' device addresses; make that
- * first call before any stream capture.  Each call copies its tables into
- * the shared arrays and waits for those copies, then launches the kernels
- * asynchronously.  All calls share the arrays, which keep the last call's
- * contents: calls whose kernels overlap on a GPU (other streams, other host
- * threads) race and must be serialised by the caller.
+ * The first call on a device looks up the arrays' device addresses (once per
+ * device, safe from several host threads).  A call whose grid, phase moduli
+ * and C0 differ from the previous call's on that device copies its tables
+ * from host memory into the arrays (stream-ordered; from pageable memory the
+ * runtime first waits for the stream's earlier work); a call with the same
+ * ones copies nothing and only launches the kernels, asynchronously.  Never
+ * call it on a stream that is being captured into a CUDA graph: such calls
+ * are refused with RPM_ERR_INVALID_ARG.  All calls share the arrays, which
+ * keep the last call's contents: calls whose kernels overlap on a GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
  * Returns RPM_ERR_INVALID_ARG / RPM_ERR_UNSUPPORTED_GRID for bad arguments,
  * RPM_ERR_CUDA if a CUDA call fails.
  */

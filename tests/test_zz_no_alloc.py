@@ -4,8 +4,9 @@ Some callers cannot allocate device memory (their host application owns the
 device memory, or they may not pay cudaMalloc's synchronisation); this entry
 point serves them from fixed file-scope scratch.  The test calls it through
 the C ABI twice in a row and compares each result with rpm_apply_gamma, the
-context-based entry point, within the Gamma0-apply tolerance of the other
-tests.  The file is named to be collected last.
+context-based entry point, and with the FP64 oracle's map, within the
+Gamma0-apply tolerance of the other tests.  The file is named to be
+collected last.
 """
 import ctypes
 
@@ -13,6 +14,7 @@ import numpy as np
 import pytest
 
 import microstructure as ms
+from oracle import rpm_oracle as o
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -62,8 +64,29 @@ def test_noalloc_matches_context_entry_point():
                 torch.cuda.synchronize()
                 err = (torch.linalg.vector_norm(got - ref) / torch.linalg.vector_norm(ref)).item()
                 assert err < TOL, (shape, call, flags, err)
+                prob = o.Problem.from_cell(cell)
+                xh = x.cpu().numpy().astype(np.float64)
+                want = (o.apply_F(prob, xh, E) if flags == rpm.RPM_GAMMA_FULL_MAP
+                        else o.apply_F(prob, xh, np.zeros(6)))
+                gh = got.cpu().numpy().astype(np.float64)
+                err_o = np.linalg.norm(gh - want) / np.linalg.norm(want)
+                assert err_o < TOL, (shape, call, flags, err_o)
     # sizes beyond the fixed scratch are refused
     big = rpm.rpm_grid(128, 128, 128, 1.0, 1.0, 1.0)
     st = L.rpm_apply_gamma_noalloc(ctypes.byref(big), phase_d.data_ptr(), len(phases), iso, c0,
                                    x.data_ptr(), Ec, got.data_ptr(), 0, None)
     assert st == rpm.RPM_ERR_UNSUPPORTED_GRID
+    # planes that are not square are refused (the fixed scratch serves the
+    # three-pass kernels only)
+    rect = rpm.rpm_grid(64, 32, 32, 1.0, 1.0, 1.0)
+    st = L.rpm_apply_gamma_noalloc(ctypes.byref(rect), phase_d.data_ptr(), len(phases), iso, c0,
+                                   x.data_ptr(), Ec, got.data_ptr(), 0, None)
+    assert st == rpm.RPM_ERR_UNSUPPORTED_GRID
+    # a stream under graph capture is refused before any CUDA work is issued
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        x.add_(0.0)
+        st_cap = L.rpm_apply_gamma_noalloc(ctypes.byref(grid), phase_d.data_ptr(), len(phases),
+                                           iso, c0, x.data_ptr(), Ec, got.data_ptr(), 0,
+                                           torch.cuda.current_stream().cuda_stream)
+    assert st_cap == rpm.RPM_ERR_INVALID_ARG
