@@ -2,7 +2,7 @@
 reference arm.  Calls only oracle/ (and the seeded input generators).
 
   python tests/golden/make_golden.py softincl128_warm   # ~10 min on one core
-  python tests/golden/make_golden.py stiff64            # ~7 min on one core
+  python tests/golden/make_golden.py stiff64            # ~10 min on one core
   python tests/golden/make_golden.py softincl128        # cold form: more than 4 h
                                                         # on one core (not stored)
 """
@@ -76,9 +76,15 @@ def stiff64():
         t0 = time.time()
         r = o.rpm_solve(prob, E, o.Options(tol=1e-8, p_max=20, n_max=10, max_iters=1500))
         r6 = next(i for i, v in enumerate(r.residuals) if v <= 1e-6)
+        # the same solve stopped at tol 1e-6: how far a 1e-6 answer of the
+        # method itself lies from the converged one
+        s6 = o.rpm_solve(prob, E, o.Options(tol=1e-6, p_max=20, n_max=10, max_iters=1500))
         out[str(seed)] = {"status": r.status, "iters": r.iters, "residual": r.residual,
                           "iters_to_1e-6": r6, "E": list(map(float, E)),
                           "mean_stress": list(map(float, r.mean_stress)),
+                          "tol_1e-6": {"status": s6.status, "iters": s6.iters,
+                                       "residual": s6.residual,
+                                       "mean_stress": list(map(float, s6.mean_stress))},
                           "seconds_one_core": time.time() - t0}
     with open(os.path.join(HERE, "stiff64_oracle_solve.json"), "w") as f:
         json.dump(out, f, indent=1)

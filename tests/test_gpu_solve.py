@@ -347,7 +347,12 @@ def test_stiff_cell_converges_and_matches_oracle_golden(rpm, seed):
     RPM iteration stalled above 1e-6 (5012) or diverged after a late basis
     growth from a non-trivial start (5013).  With the growth noise guard and
     re-centring after a stall it converges, within twice the oracle's steps,
-    to the FP64 oracle's answer (solved to 1e-8 in tests/golden)."""
+    to the FP64 oracle's answer (solved to 1e-8 in tests/golden) within the
+    effective-stiffness tolerance.  The oracle's own answer at tol 1e-6 lies
+    within 2e-6 of its 1e-8 answer on these cells (stored beside it), so the
+    method's tolerance is not what separates the two: the float32 fixed point
+    itself sits 8e-6 (5012) and 3e-6 (5013) from the FP64 one, at tol 1e-6 as
+    at 1e-8."""
     import json
     import os
     g = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
@@ -359,8 +364,10 @@ def test_stiff_cell_converges_and_matches_oracle_golden(rpm, seed):
     assert info["converged"], info
     assert info["iters"] <= 2 * g["iters_to_1e-6"], (info["iters"], g["iters_to_1e-6"])
     ref = np.array(g["mean_stress"])
+    spread = (np.max(np.abs(np.array(g["tol_1e-6"]["mean_stress"]) - ref)) / np.max(np.abs(ref)))
+    assert spread < 1e-5, spread
     err = np.max(np.abs(np.array(info["mean_stress"]) - ref)) / np.max(np.abs(ref))
-    assert err < 5e-4, err
+    assert err < CEFF_TOL, err
 
 
 def test_ellipsoids_256_warm_form_converges_within_bounds(rpm):
