@@ -194,6 +194,33 @@ def oracle_sample(cell, iters_sample: int = 2) -> dict:
     return {"seconds": dt, "f_applies": r.f_applies, "sec_per_f": dt / max(r.f_applies, 1)}
 
 
+def _oracle_sample_worker(args):
+    """One process of the all-core oracle sample: builds the benchmark cell
+    itself (seeded, so every process solves the same cell) and times the
+    bounded oracle sample on it."""
+    n, seed, e_incl, iters = args
+    cell = ms.cell_nearvoid(n, seed, c0_scale=1.0, e_incl=e_incl)
+    return oracle_sample(cell, iters)
+
+
+def oracle_sample_all_cores(iters: int, workers: int) -> dict:
+    """The bounded oracle sample run by `workers` processes at once (one
+    independent copy of the same solve per host core; processes started with
+    spawn, after CUDA was initialised in this process): F applications per
+    second of the whole host."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(workers) as pool:
+        res = pool.map(_oracle_sample_worker, [(N, 0, E_INCL, iters)] * workers)
+    wall = time.perf_counter() - t0
+    f_total = sum(r["f_applies"] for r in res)
+    busy = max(r["seconds"] for r in res)
+    return {"workers": workers, "f_applies": f_total, "seconds_max_worker": busy,
+            "wall_s_incl_startup": wall, "f_per_s": f_total / busy,
+            "sec_per_f_per_worker": statistics.median(r["sec_per_f"] for r in res)}
+
+
 def oracle_reference_iters(form: str = "warm") -> int | None:
     """F applications of the oracle's own converged solve of the workload, in
     the headline form (stored by tests/golden/make_golden.py, oracle only)."""
@@ -273,6 +300,62 @@ def time_solves(ctx, E, steps, warmup, stream, flush, eps_out, raise_ok=True):
     return sum(a.elapsed_time(b) for a, b in ev), infos
 
 
+def kernel_classes(infos, n_vox: int, pk: dict) -> dict:
+    """Rooflines of the two kernel classes of a set of solves, from the CUDA
+    events the library records around every launch group (opt.profile): the
+    Gamma0 application (algorithmic 49 B/voxel per application) and the
+    projections (the bytes the library counts for each dots/combine launch)."""
+    gamma_ms = sum(i["gamma_ms"] for i in infos)
+    n_gamma = sum(i["gamma_applies"] for i in infos)
+    proj_ms = sum(i["proj_ms"] for i in infos)
+    proj_bytes = sum(i["proj_bytes"] for i in infos)
+    t_gamma = gamma_ms / max(n_gamma, 1) / 1e3
+    alg_gamma = BYTES_PER_VOXEL_GAMMA * n_vox
+    ach_gamma = alg_gamma / t_gamma / 1e9 if t_gamma > 0 else 0.0
+    ach_proj = proj_bytes / (proj_ms / 1e3) / 1e9 if proj_ms > 0 else 0.0
+    gamma_line = {"bound": "hbm",
+                  "kernel": "gamma_apply (pass A+B+C: one F application; in the warm-start stage "
+                            "with Algorithm 3's post-step)",
+                  "achieved": round(ach_gamma, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                  "frac": round(ach_gamma / pk["hbm_gbs"], 4),
+                  "algorithmic_bytes_per_launch": alg_gamma,
+                  "avg_launch_ms": round(t_gamma * 1e3, 4), "launches": n_gamma,
+                  "total_ms": round(gamma_ms, 3)}
+    proj_line = {"bound": "hbm", "kernel": "projections (k_dots + k_reduce + k_combine)",
+                 "achieved": round(ach_proj, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                 "frac": round(ach_proj / pk["hbm_gbs"], 4), "traffic": None,
+                 "algorithmic_bytes_per_solve": proj_bytes / max(len(infos), 1),
+                 "total_ms": round(proj_ms, 3)}
+    return {"gamma_apply": gamma_line, "projections": proj_line}
+
+
+NEARVOID_C0 = (0.25, 0.5, 1.0, 2.0)
+NEARVOID_BUDGET = 1000      # RPM steps (and warm-start steps) per solve of the sweep
+
+
+def nearvoid_sweep(rpm, stream) -> dict:
+    """The near-void cell itself (inclusion E = 1e-6) with C0 at 0.25, 0.5, 1
+    and 2 x the matrix moduli, cold and warm-started, each solve capped at a
+    fixed step budget: status, steps, increment reached."""
+    E = ms.unit_strain(0)
+    rows = []
+    for scale in NEARVOID_C0:
+        cell = ms.cell_nearvoid(N, 0, c0_scale=scale, e_incl=1e-6)
+        for form in ("cold", "warm"):
+            kw = dict(tol=TOL, p_max=P_MAX, n_max=10, max_iters=NEARVOID_BUDGET)
+            if form == "warm":
+                kw.update(warm_tol=WARM_TOL, warm_max_iters=NEARVOID_BUDGET)
+            with rpm.Context(cell, rpm.rpm_default_options(**kw), stream=stream) as ctx:
+                st, info = ctx.solve(E, raise_on_failure=False)
+            rows.append({"c0_scale": scale, "form": form, "status": rpm.status_name(st),
+                         "iters": info["iters"], "warm_iters": info["warm_iters"],
+                         "basis": info["basis_size"], "residual0": info["residual0"],
+                         "residual": info["residual"], "F": info["gamma_applies"],
+                         "ms": round(info["ms"], 2)})
+    return {"cell": "128^3 RSA spheres r 6-12 vox (seed 0), vf 0.20, E_incl 1e-6, matrix E 1",
+            "budget_steps": NEARVOID_BUDGET, "tol": TOL, "load": "e11", "rows": rows}
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_info()
@@ -323,38 +406,21 @@ def run_ours(args):
 
     # Kernel classes and their rooflines, from CUDA events the library records
     # on this stream around every launch group during the timed steps.
-    gamma_ms = sum(i["gamma_ms"] for i in infos)
-    n_gamma = sum(i["gamma_applies"] for i in infos)
-    proj_ms = sum(i["proj_ms"] for i in infos)
-    proj_bytes = sum(i["proj_bytes"] for i in infos)
     launches = sum(i["launches"] for i in infos)
     pk = peaks()
-    t_gamma = gamma_ms / max(n_gamma, 1) / 1e3
-    alg_gamma = BYTES_PER_VOXEL_GAMMA * N ** 3
-    ach_gamma = alg_gamma / t_gamma / 1e9
-    ach_proj = proj_bytes / (proj_ms / 1e3) / 1e9 if proj_ms > 0 else 0.0
-    gamma_line = {"bound": "hbm",
-                  "kernel": "gamma_apply (pass A+B+C: one F application; in the warm-start stage "
-                            "with Algorithm 3's post-step)",
-                  "achieved": round(ach_gamma, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
-                  "frac": round(ach_gamma / pk["hbm_gbs"], 4),
-                  "traffic": recorded_traffic("gamma_apply_128"),
-                  "dram_gbs_from_traffic": (round(recorded_traffic("gamma_apply_128") / t_gamma / 1e9, 1)
-                                            if recorded_traffic("gamma_apply_128") else None),
-                  "algorithmic_bytes_per_launch": alg_gamma,
-                  "avg_launch_ms": round(t_gamma * 1e3, 4)}
-    proj_line = {"bound": "hbm", "kernel": "projections (k_dots + k_reduce + k_combine)",
-                 "achieved": round(ach_proj, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
-                 "frac": round(ach_proj / pk["hbm_gbs"], 4), "traffic": None,
-                 "algorithmic_bytes_per_step": proj_bytes / max(len(infos), 1),
-                 "total_ms": round(proj_ms, 3)}
-    dominant = proj_line if proj_ms >= gamma_ms else gamma_line
+    classes = kernel_classes(infos, N ** 3, pk)
+    gamma_line, proj_line = classes["gamma_apply"], classes["projections"]
+    tr = recorded_traffic("gamma_apply_128")
+    gamma_line["traffic"] = tr
+    gamma_line["dram_gbs_from_traffic"] = (round(tr / (gamma_line["avg_launch_ms"] / 1e3) / 1e9, 1)
+                                           if tr else None)
+    dominant = proj_line if proj_line["total_ms"] >= gamma_line["total_ms"] else gamma_line
     roofline = dict(dominant)
     roofline.update({"peak_src": pk["src"],
-                     "time_share": {"gamma_ms": round(gamma_ms, 3),
-                                    "projection_ms": round(proj_ms, 3),
+                     "time_share": {"gamma_ms": gamma_line["total_ms"],
+                                    "projection_ms": proj_line["total_ms"],
                                     "solve_ms": round(dev_ms, 3)},
-                     "classes": {"gamma_apply": gamma_line, "projections": proj_line}})
+                     "classes": classes})
 
     # the cold-start form on the same cell, same timing (comparison inside the line)
     cold = None
@@ -367,7 +433,9 @@ def run_ours(args):
                 "ms_per_step": round(c_ms / c_steps, 3), "iters": c_inf[0]["iters"],
                 "basis_size": c_inf[0]["basis_size"],
                 "mean_stress_11": c_inf[0]["mean_stress"][0],
-                "oracle_rel_err": oracle_error("cold", c_inf[0]["mean_stress"])}
+                "oracle_rel_err": oracle_error("cold", c_inf[0]["mean_stress"]),
+                "launches_per_solve": c_inf[0]["launches"],
+                "roofline_classes": kernel_classes(c_inf, N ** 3, pk)}
 
     # the same form with the RPM stage's reference medium at 2x the matrix
     c0x2 = None
@@ -381,6 +449,11 @@ def run_ours(args):
                 "iters": c2_inf[0]["iters"], "warm_iters": c2_inf[0]["warm_iters"],
                 "gamma_applies": c2_inf[0]["gamma_applies"],
                 "mean_stress_11": c2_inf[0]["mean_stress"][0]}
+
+    # BASELINE config 2 itself: the near-void cell at the four reference media
+    nearvoid = None
+    if args.form == "warm" and not args.no_cold and world == 1:
+        nearvoid = nearvoid_sweep(rpm, stream)
 
     # end to end through the C ABI with host buffers: phase map in, strain field out
     phase_host = np.ascontiguousarray(cell.phase)
@@ -398,13 +471,19 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        s = oracle_sample(cell, CPU_SAMPLE_ITERS)
         nF_gpu = statistics.median(i["gamma_applies"] for i in infos)
-        cpu = {"value": 1.0 / (s["sec_per_f"] * nF_gpu), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"oracle RPM solve of this cell bounded to {CPU_SAMPLE_ITERS} iterations "
-                         f"({s['f_applies']} F "
-                         f"applications, {s['seconds']:.1f} s on 1 host core); scaled by the "
-                         f"{nF_gpu:g} F applications of the GPU solve"}
+        s1 = oracle_sample(cell, CPU_SAMPLE_ITERS)
+        ncores = os.cpu_count() or 1
+        sa = oracle_sample_all_cores(CPU_SAMPLE_ITERS, ncores)
+        cpu = {"value": sa["f_per_s"] / nF_gpu, "unit": UNIT, "cores": ncores, "kind": "oracle",
+               "sample": f"{ncores} host processes (one per core, os.cpu_count() = {ncores}), each "
+                         f"the oracle RPM solve of this cell bounded to {CPU_SAMPLE_ITERS} "
+                         f"iterations ({sa['f_applies']} F applications in all, slowest process "
+                         f"{sa['seconds_max_worker']:.1f} s); F applications per second of the "
+                         f"whole host divided by the {nF_gpu:g} F applications of the GPU solve",
+               "one_core": {"value": 1.0 / (s1["sec_per_f"] * nF_gpu), "unit": UNIT, "cores": 1,
+                            "sample": f"the same bounded solve in this process alone "
+                                      f"({s1['f_applies']} F applications, {s1['seconds']:.1f} s)"}}
     ctx.close()
     if rank == 0:
         form = ("warm-started: Algorithm 3 (Accelerated, alpha = beta = 2, C0 at the geometric "
@@ -425,6 +504,7 @@ def run_ours(args):
                     "mean_stress_11": infos[0]["mean_stress"][0],
                     "cold_start": cold,
                     "c0_2x_matrix": c0x2,
+                    "nearvoid_1e-6_c0_sweep": nearvoid,
                     "oracle_rel_err": oracle_error(args.form, infos[0]["mean_stress"]),
                     "parallelism": f"replicas x{world}"}),
                 "roofline": roofline, "cpu_baseline": cpu,
@@ -513,6 +593,39 @@ def run_study_fibre2d(args):
             print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
     print(json.dumps({"study": "fibre2d", "grid": [256, 256, 1], "load": "E12 = 0.005",
                       "tol": args.study_tol, "rows": rows}), flush=True)
+
+
+NMAX_SWEEP = (1, 2, 5, 10, 20, 50)
+
+
+def run_study_nmax(args):
+    """Section 5.2 setting: RPM on the 2D fibre cell (256^2, C0 = mean,
+    p_max 20) with the growth interval n_max in {1, 2, 5, 10, 20, 50} at
+    contrast K = 50 and 1e3: steps, final basis size and device time to the
+    increment tolerance.  Prints one JSON line."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as entry
+    entry.build()
+    from paper_2003_07720_gb300 import rpm
+    E = np.zeros(6)
+    E[5] = 0.005
+    rows = []
+    for K in (50.0, 1e3):
+        cell = ms.cell_fibre2d(256, K, c0="mean")
+        for nmax in NMAX_SWEEP:
+            opts = rpm.rpm_default_options(tol=args.study_tol, max_iters=20000, p_max=20,
+                                           n_max=nmax)
+            with rpm.Context(cell, opts) as ctx:
+                ctx.solve(E, raise_on_failure=False)          # warm-up (kernel attributes)
+                st, info = ctx.solve(E, raise_on_failure=False)
+            rows.append({"K": K, "n_max": nmax, "status": rpm.status_name(st),
+                         "iters": info["iters"], "basis": info["basis_size"],
+                         "F": info["gamma_applies"], "ms": round(info["ms"], 2),
+                         "sigma12": info["mean_stress"][5], "residual": info["residual"]})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    print(json.dumps({"study": "nmax", "grid": [256, 256, 1], "load": "E12 = 0.005",
+                      "tol": args.study_tol, "p_max": 20, "rows": rows}), flush=True)
 
 
 def run_study_batch(args):
@@ -708,7 +821,7 @@ def main():
     ap.add_argument("--fno-batch", type=int, default=8)
     ap.add_argument("--fno-lr", type=float, default=2e-3)
     ap.add_argument("--fno-save", default="", help="write the trained parameters (.npy)")
-    ap.add_argument("--study", default=None, choices=[None, "fibre2d", "batch", "fno"],
+    ap.add_argument("--study", default=None, choices=[None, "fibre2d", "nmax", "batch", "fno"],
                     help="run a study instead of the benchmark")
     ap.add_argument("--study-tol", type=float, default=1e-6)
     ap.add_argument("--grid", type=int, default=N, help="cube size for --kernel gamma "
@@ -720,6 +833,8 @@ def main():
     args = ap.parse_args()
     if args.study == "fibre2d":
         run_study_fibre2d(args)
+    elif args.study == "nmax":
+        run_study_nmax(args)
     elif args.study == "batch":
         run_study_batch(args)
     elif args.study == "fno":

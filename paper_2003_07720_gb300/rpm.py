@@ -302,6 +302,11 @@ def rpm_destroy(ctx) -> None:
         lib().rpm_destroy(ctx)
 
 
+def status_name(status: int) -> str:
+    """Name of a status code (rpm_status_string)."""
+    return lib().rpm_status_string(int(status)).decode()
+
+
 class Context:
     """Owning wrapper around a context handle (closes on `close()` / exit)."""
 
