@@ -391,14 +391,17 @@ __global__ void __launch_bounds__(kPlaneThreads, Split<NX / 2>::N1 >= 16 ? 2 : k
   static_assert(X2 > 1 && X1 % 2 == 0, "x split must have two steps and an even first factor");
   extern __shared__ __align__(128) float2 sm[];
   float2* P = sm;                      // [NY][SX]: the spectrum plane's own layout
-  float2* twx = P + NY * SX;
+  float2* twx = P + NY * SX;           // transposed: W^(n2 k1) at k1 * X2 + n2
   float2* twy = twx + NXH;
   float2* r2c = twy + NY;
   float2* dm = r2c + SX;
   const int c = blockIdx.x, z = blockIdx.y;
-  for (int i = threadIdx.x; i < NXH; i += blockDim.x) twx[i] = g.tw_x[i];
+  allow_dependent_launch();
+  for (int i = threadIdx.x; i < NXH; i += blockDim.x)
+    twx[(i % X1) * X2 + i / X1] = g.tw_x[i];
   for (int i = threadIdx.x; i < NY; i += blockDim.x) twy[i] = g.tw_y[i];
   for (int i = threadIdx.x; i < SX; i += blockDim.x) r2c[i] = g.r2c_w[i];
+  grid_dependency_wait();   // the FFT tables are fixed; everything below may be in flight
   for (int i = threadIdx.x; i < 256; i += blockDim.x) dm[i] = g.dmat[i];
   __syncthreads();
   const size_t nf2 = (size_t)g.n / 2;
@@ -452,7 +455,7 @@ __global__ void __launch_bounds__(kPlaneThreads, Split<NX / 2>::N1 >= 16 ? 2 : k
     }
     RegDft<X1, false>::run(v);
 #pragma unroll
-    for (int k1 = 1; k1 < X1; ++k1) v[k1] = cmul(v[k1], twx[n2 * X1 + k1]);
+    for (int k1 = 1; k1 < X1; ++k1) v[k1] = cmul(v[k1], twx[k1 * X2 + n2]);
     float2* p = P + y * SX + n2;
 #pragma unroll
     for (int i = 0; i < X1; ++i) p[i * X2] = v[i];
@@ -585,16 +588,20 @@ __global__ void __launch_bounds__(kPlaneThreads, kPlaneMinBlocks)
   __shared__ __align__(8) uint64_t bar;
   __shared__ int fail;
   const int item = blockIdx.x;   // c * nz + z
+  allow_dependent_launch();
   if (threadIdx.x == 0) {
     fail = 0;
     mbar_init(&bar, 1);
     mbar_init_fence();
-    mbar_arrive_expect_tx(&bar, PL * 8);
-    bulk_load(P, spec + (size_t)item * g.plane, PL * 8, &bar);
   }
   for (int i = threadIdx.x; i < NXH; i += blockDim.x) twx[i] = g.tw_x[i];
   for (int i = threadIdx.x; i < NY; i += blockDim.x) twy[i] = g.tw_y[i];
   for (int i = threadIdx.x; i < SX; i += blockDim.x) r2c[i] = g.r2c_w[i];
+  grid_dependency_wait();
+  if (threadIdx.x == 0) {
+    mbar_arrive_expect_tx(&bar, PL * 8);
+    bulk_load(P, spec + (size_t)item * g.plane, PL * 8, &bar);
+  }
   __syncthreads();
   if (!mbar_wait(&bar, 0)) fail = 1;
   __syncthreads();
@@ -747,6 +754,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_pencil_green(GridDev g, float2*
   __shared__ float4 pen[T];             // per pencil: (xi_x, xi_y, has-Nyquist, non-zero count)
   const int m0 = blockIdx.x * T;
   const int plane = g.plane;
+  allow_dependent_launch();
   for (int i = threadIdx.x; i < NZ; i += blockDim.x) twz[i] = g.tw_z[i];
   if (threadIdx.x < T) {
     const int m = m0 + threadIdx.x;
@@ -760,6 +768,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_pencil_green(GridDev g, float2*
     }
     pen[threadIdx.x] = q;
   }
+  grid_dependency_wait();
   __syncthreads();
   // forward step 1; task q -> (pencil t fastest, then component, then n2):
   // a half-warp covers two components, whose lines are 16 words apart in banks
@@ -1164,6 +1173,24 @@ static cudaError_t launch_ypencil(const GridDev& g, float2* spec, bool inv, cuda
 #define RPM_FUSED_PLANE_SIZES(X) X(48) X(64) X(96) X(128)
 #define RPM_FUSED_Z_SIZES(X) X(32) X(48) X(64) X(96) X(128)
 
+// Launch with programmatic stream serialization: the kernel may begin (its
+// fixed-table prologue) while the previous kernel of the stream finishes.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, int threads, size_t smem,
+                              cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <int NX>
 static cudaError_t launch_fused_plane(const GridDev& g, const float* in, float* out, float2* spec,
                                       int mode, int which, cudaStream_t st) {
@@ -1173,14 +1200,12 @@ static cudaError_t launch_fused_plane(const GridDev& g, const float* in, float* 
   cudaError_t e;
   if (which == 0) {
     if ((e = set_smem(k_plane_fwd<NX, NX>, smem + 256 * sizeof(float2))) != cudaSuccess) return e;
-    k_plane_fwd<NX, NX><<<dim3(6, g.nz), kPlaneThreads, smem + 256 * sizeof(float2), st>>>(
-        g, in, spec, mode);
-  } else {
-    if ((e = set_smem(k_plane_inv<NX, NX>, smem)) != cudaSuccess) return e;
-    k_plane_inv<NX, NX><<<6 * g.nz, kPlaneThreads, smem, st>>>(g, spec, out,
-                                                               1.0f / (float)g.n);
+    return launch_pdl(k_plane_fwd<NX, NX>, dim3(6, g.nz), kPlaneThreads,
+                      smem + 256 * sizeof(float2), st, g, in, spec, mode);
   }
-  return cudaGetLastError();
+  if ((e = set_smem(k_plane_inv<NX, NX>, smem)) != cudaSuccess) return e;
+  return launch_pdl(k_plane_inv<NX, NX>, dim3(6 * g.nz), kPlaneThreads, smem, st, g,
+                    (const float2*)spec, out, 1.0f / (float)g.n);
 }
 
 template <int NZ>
@@ -1190,8 +1215,8 @@ static cudaError_t launch_fused_pencil(const GridDev& g, float2* spec, int mode,
   const size_t smem = (size_t)(6 * C::T * C::NZP + NZ) * sizeof(float2);
   cudaError_t e;
   if ((e = set_smem(k_pencil_green<NZ>, smem)) != cudaSuccess) return e;
-  k_pencil_green<NZ><<<(g.plane + C::T - 1) / C::T, kThreads, smem, st>>>(g, spec, mode, ga);
-  return cudaGetLastError();
+  return launch_pdl(k_pencil_green<NZ>, dim3((g.plane + C::T - 1) / C::T), kThreads, smem, st, g,
+                    spec, mode, ga);
 }
 
 static bool fused_plane_ok(const GridDev& g, const float2* spec) {
