@@ -680,6 +680,54 @@ def run_study_batch(args):
     print(json.dumps(out), flush=True)
 
 
+def run_study_c4(args):
+    """The batched effective-stiffness sweep as specified: 96 seeded cells
+    (grids 32^3, 48^3, 64^3, 96^3 by seed mod 4; spheres to a volume fraction
+    U(0.1, 0.35); inclusion contrast 10^U(-6, 3); C0 = mean) x 6 unit loads
+    through rpm_effective_stiffness_batch (worker streams), each solve capped
+    at a step budget.  Reports solves/s and, per cell, the status of every
+    load, the steps and the 6 x 6 C_eff.  Prints one JSON line."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as entry
+    entry.build()
+    from paper_2003_07720_gb300 import rpm
+    cells = [ms.cell_batch_member(s) for s in range(args.c4_cells)]
+    budget = args.c4_budget
+    forms = {"cold": rpm.rpm_default_options(tol=TOL, p_max=P_MAX, max_iters=budget),
+             "warm": rpm.rpm_default_options(tol=TOL, p_max=P_MAX, max_iters=budget,
+                                             warm_tol=WARM_TOL, warm_max_iters=budget)}
+    rpm.rpm_effective_stiffness_batch(cells[:1], forms["cold"], n_workers=1,
+                                      raise_on_failure=False)      # warm-up
+    torch.cuda.synchronize()
+    out = {"study": "c4", "cells": len(cells), "loads": 6, "budget_steps": budget, "tol": TOL,
+           "workers": args.batch_workers}
+    for name, opts in forms.items():
+        t0 = time.perf_counter()
+        C, infos, stat, st = rpm.rpm_effective_stiffness_batch(cells, opts,
+                                                               n_workers=args.batch_workers,
+                                                               raise_on_failure=False)
+        dt = time.perf_counter() - t0
+        rows = []
+        for i, c in enumerate(cells):
+            inf = infos[i]
+            rows.append({"seed": i, "grid": int(c.shape[0]),
+                         "contrast": float(c.mu[1] / c.mu[0]),
+                         "volume_fraction": round(float(c.phase.mean()), 4),
+                         "status": rpm.status_name(stat[i]),
+                         "converged_loads": int(sum(1 for j in inf if j["converged"])),
+                         "steps": [int(j["iters"]) for j in inf],
+                         "C_eff": [[float("%.7g" % v) for v in row] for row in C[i]]})
+        conv = [r for r in rows if r["converged_loads"] == 6]
+        out[name] = {"seconds": round(dt, 3), "solves_per_s": round(6 * len(cells) / dt, 2),
+                     "cells_all_loads_converged": len(conv),
+                     "solves_converged": int(sum(r["converged_loads"] for r in rows)),
+                     "rows": rows}
+        print(json.dumps({k: v for k, v in out[name].items() if k != "rows"}), file=sys.stderr,
+              flush=True)
+    print(json.dumps(out), flush=True)
+
+
 def fno_flops_per_sample(n: int, m: int, layers: int, width: int = 16) -> dict:
     """Algorithmic FLOPs of one sample through the spectral neural operator
     (truncated DFT stages as sums over N points per kept frequency; a real x
@@ -718,7 +766,7 @@ def run_fno_kernel(args):
     E = np.stack([ms.strain_direction(i) for i in range(B)])
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    with fno.Fno(n, m, L, max_batch=B, stream=stream) as net:
+    with fno.Fno(n, m, L, max_batch=B, stream=stream, precision=args.fno_precision) as net:
         net.set_params(ms.fno_params(m, L, seed=0))
         for _ in range(args.warmup):
             net.loss_grad(feat, E, tgt)
@@ -734,7 +782,8 @@ def run_fno_kernel(args):
     t = statistics.median(ts) / 1e3
     fl = fno_flops_per_sample(n, m, L)
     ach = fl["train"] * B / t / 1e12
-    print(json.dumps({"kernel": "fno_loss_grad", "grid": [n, n, n], "batch": B, "modes": m,
+    print(json.dumps({"kernel": "fno_loss_grad", "precision": args.fno_precision,
+                      "grid": [n, n, n], "batch": B, "modes": m,
                       "layers": L, "median_ms": round(t * 1e3, 4),
                       "all_ms": [round(v, 4) for v in ts],
                       "roofline": {"bound": "alu", "achieved": round(ach, 2),
@@ -760,7 +809,7 @@ def run_study_fno(args):
     data = fno_train.make_dataset(n, seeds)
     out["dataset"] = {"cells": len(seeds), "solve_seconds": round(data.solve_s, 2),
                       "converged": int(data.converged.sum()), "train_samples": len(data.seeds)}
-    net = fno.Fno(n, m, L, max_batch=B)
+    net = fno.Fno(n, m, L, max_batch=B, precision=args.fno_precision)
     net.set_params(ms.fno_params(m, L, seed=0))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -779,7 +828,7 @@ def run_study_fno(args):
     test = list(range(5000, 5000 + args.fno_test))
     res = {}
     for nn in (n, 2 * n):
-        with fno.Fno(nn, m, L, max_batch=1) as net2:
+        with fno.Fno(nn, m, L, max_batch=1, precision=args.fno_precision) as net2:
             net2.set_params(params)
             rows = fno_train.evaluate(net2, nn, test)
         summ = {}
@@ -821,13 +870,18 @@ def main():
     ap.add_argument("--fno-batch", type=int, default=8)
     ap.add_argument("--fno-lr", type=float, default=2e-3)
     ap.add_argument("--fno-save", default="", help="write the trained parameters (.npy)")
-    ap.add_argument("--study", default=None, choices=[None, "fibre2d", "nmax", "batch", "fno"],
+    ap.add_argument("--fno-precision", default="bf16", choices=["bf16", "fp32"],
+                    help="network transforms: BF16 tensor cores (default) or float32")
+    ap.add_argument("--study", default=None,
+                    choices=[None, "fibre2d", "nmax", "batch", "c4", "fno"],
                     help="run a study instead of the benchmark")
     ap.add_argument("--study-tol", type=float, default=1e-6)
     ap.add_argument("--grid", type=int, default=N, help="cube size for --kernel gamma "
                     "(the benchmark cell at 128, a laminate otherwise)")
     ap.add_argument("--batch-cells", type=int, default=16)
     ap.add_argument("--batch-workers", type=int, default=8)
+    ap.add_argument("--c4-cells", type=int, default=96)
+    ap.add_argument("--c4-budget", type=int, default=2000, help="step budget per solve")
     ap.add_argument("--kernel", default=None, choices=[None, "gamma", "fno"],
                     help="time one kernel group alone instead of the solve")
     args = ap.parse_args()
@@ -837,6 +891,8 @@ def main():
         run_study_nmax(args)
     elif args.study == "batch":
         run_study_batch(args)
+    elif args.study == "c4":
+        run_study_c4(args)
     elif args.study == "fno":
         run_study_fno(args)
     elif args.kernel == "fno":

@@ -64,11 +64,18 @@ extern "C" {
 
 typedef struct rpm_fno rpm_fno;
 
+/* Arithmetic of the network's transforms (rpm_fno_config.precision). */
+#define RPM_FNO_FP32 0  /* float32 throughout (SIMT FMA) */
+#define RPM_FNO_BF16 1  /* truncated DFT stages as BF16 tensor-core products with float32
+                           accumulation (mma.sync m16n8k16) where N % 16 == 0; everything else
+                           float32 */
+
 typedef struct {
   int n;          /* grid side N: 24..128, a multiple of 8, N >= 2 * modes */
   int modes;      /* m: 1..RPM_FNO_MAX_MODES */
   int layers;     /* L: 1..RPM_FNO_MAX_LAYERS */
   int max_batch;  /* largest batch B of any call, 1..RPM_FNO_MAX_BATCH */
+  int precision;  /* RPM_FNO_FP32 or RPM_FNO_BF16 */
 } rpm_fno_config;
 
 typedef struct {

@@ -33,6 +33,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "rpm.h"
 #include "rpm_fno.h"
 #include "rpm_internal.h"
@@ -210,6 +212,173 @@ __global__ void __launch_bounds__(kThreads) k_xy_fwd(const float* __restrict__ s
   }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core form of k_xy_fwd (configuration precision RPM_FNO_BF16): both
+// truncated DFT stages as BF16 matrix products with float32 accumulation
+// (mma.sync m16n8k16), operands staged in shared memory as bfloat16 and
+// loaded with ldmatrix.
+//   x stage  C[y][2kx + {re, im}] = sum_x v[y][x] (Tx_re, Tx_im)[x][kx]
+//            M = N rows, K = N, Nout = 2 * round4(m)
+//   y stage  D[r][kx] = sum_{y, re/im} Ay[r][2y + .] X[y][kx].(re, im), with
+//            rows r < KPY giving Re V[ky_r] (Ty_re, -Ty_im) and rows KPY + r
+//            giving Im V[ky_r] (Ty_im, Ty_re); M = 2 KPY, K = 2N, Nout = round8(m)
+// Needs N % 16 == 0.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t (&r)[2], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];"
+               : "=r"(r[0]), "=r"(r[1])
+               : "r"(smem_u32(p)));
+}
+// D += A (16 x 16, row) * B (16 x 8, col), bfloat16 in, float32 accumulate
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4],
+                                         const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+__device__ __forceinline__ uint16_t bf16_bits(float x) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+__device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
+  return (uint32_t)bf16_bits(lo) | ((uint32_t)bf16_bits(hi) << 16);
+}
+
+__host__ __device__ inline int round_up(int v, int q) { return (v + q - 1) / q * q; }
+
+struct XyTc {
+  int G, NPB, NX2, KPY, MY, MPY, KPB;
+  __host__ __device__ XyTc(int N, int m) {
+    G = N <= 64 ? 4 : 1;
+    NPB = N + 8;                 // bf16 row stride of the staged planes (16-byte rows)
+    NX2 = 2 * round_up(m, 4);    // x-stage output columns
+    KPY = round_up(2 * m, 8);    // kept ky rows per part
+    MY = 2 * KPY;
+    MPY = round_up(m, 8);        // y-stage output columns (kx)
+    KPB = 2 * N + 8;             // bf16 row stride of Ay and XT
+  }
+  __host__ __device__ size_t bytes(int N) const {
+    return (size_t)2 * ((size_t)G * N * NPB + (size_t)NX2 * NPB + (size_t)MY * KPB +
+                        (size_t)G * MPY * KPB) +
+           (size_t)4 * G * MY * MPY;
+  }
+};
+size_t xy_tc_smem(int N, int m) { return XyTc(N, m).bytes(N); }
+
+// Templated on the grid side so that the index arithmetic divides by constants.
+template <int N>
+__global__ void __launch_bounds__(kThreads, 2) k_xy_fwd_tc(const float* __restrict__ src,
+                                                        float2* __restrict__ dst,
+                                                        const float2* __restrict__ twg, int m) {
+  extern __shared__ float4 smem4[];
+  const XyTc c(N, m);
+  const int ncol = 2 * m * m;
+  uint16_t* planes = reinterpret_cast<uint16_t*>(smem4);          // [G][N][NPB]
+  uint16_t* BTx = planes + (size_t)c.G * N * c.NPB;                // [NX2][NPB]
+  uint16_t* Ay = BTx + (size_t)c.NX2 * c.NPB;                      // [MY][KPB]
+  uint16_t* XT = Ay + (size_t)c.MY * c.KPB;                        // [G][MPY][KPB]
+  float* Ds = reinterpret_cast<float*>(XT + (size_t)c.G * c.MPY * c.KPB);   // [G][MY][MPY]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int z = blockIdx.x, b = blockIdx.y;
+  const long long NN = (long long)N * N;
+  float2* d = dst + ((long long)b * N + z) * ncol * W;
+  for (int i = tid; i < c.NX2 * N; i += kThreads) {
+    const int r = i / N, x = i - r * N, kx = r >> 1;
+    float v = 0.f;
+    if (kx < m) {
+      const float2 t = twg[(kx * x) % N];
+      v = (r & 1) ? t.y : t.x;
+    }
+    BTx[r * c.NPB + x] = bf16_bits(v);
+  }
+  for (int i = tid; i < c.KPY * N; i += kThreads) {
+    const int r = i / N, y = i - r * N;
+    float tr = 0.f, ti = 0.f;
+    if (r < 2 * m) {
+      const float2 t = twg[(kfreq(r, m, N) * y) % N];
+      tr = t.x;
+      ti = t.y;
+    }
+    uint16_t* re = Ay + (size_t)r * c.KPB + 2 * y;
+    uint16_t* im = Ay + (size_t)(c.KPY + r) * c.KPB + 2 * y;
+    re[0] = bf16_bits(tr);
+    re[1] = bf16_bits(-ti);
+    im[0] = bf16_bits(ti);
+    im[1] = bf16_bits(tr);
+  }
+  const int nmt = N / 16, nnt = c.NX2 / 8;          // x-stage tiles per channel
+  const int ymt = c.MY / 16, ynt = c.MPY / 8;        // y-stage tiles per channel
+  for (int c0 = 0; c0 < W; c0 += c.G) {
+    __syncthreads();   // tables written; the previous group's readers are done
+    for (int i = tid; i < c.G * N * N / 4; i += kThreads) {
+      const int g = i / (N * N / 4), r = i - g * (N * N / 4);
+      const int y = r / (N / 4), x = 4 * (r - y * (N / 4));
+      const float4 v = *reinterpret_cast<const float4*>(
+          src + (((long long)b * W + c0 + g) * N + z) * NN + (long long)y * N + x);
+      uint2 pk;
+      pk.x = bf16x2_bits(v.x, v.y);
+      pk.y = bf16x2_bits(v.z, v.w);
+      *reinterpret_cast<uint2*>(planes + ((size_t)g * N + y) * c.NPB + x) = pk;
+    }
+    __syncthreads();
+    for (int tile = warp; tile < c.G * nmt * nnt; tile += kThreads / 32) {
+      const int g = tile / (nmt * nnt), r = tile - g * (nmt * nnt);
+      const int mt = r / nnt, nt = r - mt * nnt;
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      const uint16_t* pa = planes + ((size_t)g * N + 16 * mt + (lane & 15)) * c.NPB + (lane >> 4) * 8;
+      const uint16_t* pb = BTx + (size_t)(8 * nt + (lane & 7)) * c.NPB + ((lane >> 3) & 1) * 8;
+      for (int k0 = 0; k0 < N; k0 += 16) {
+        uint32_t a[4], bb[2];
+        ldsm_x4(a, pa + k0);
+        ldsm_x2(bb, pb + k0);
+        mma_bf16(acc, a, bb);
+      }
+      // acc: rows y = 16 mt + lane/4 (and + 8), columns 2t, 2t + 1 = (re, im) of kx = 4 nt + t
+      const int y = 16 * mt + (lane >> 2), kx = 4 * nt + (lane & 3);
+      uint32_t* xt = reinterpret_cast<uint32_t*>(XT + ((size_t)g * c.MPY + kx) * c.KPB);
+      xt[y] = bf16x2_bits(acc[0], acc[1]);
+      xt[y + 8] = bf16x2_bits(acc[2], acc[3]);
+    }
+    __syncthreads();
+    for (int tile = warp; tile < c.G * ymt * ynt; tile += kThreads / 32) {
+      const int g = tile / (ymt * ynt), r = tile - g * (ymt * ynt);
+      const int mt = r / ynt, nt = r - mt * ynt;
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      const uint16_t* pa = Ay + (size_t)(16 * mt + (lane & 15)) * c.KPB + (lane >> 4) * 8;
+      const uint16_t* pb = XT + ((size_t)g * c.MPY + 8 * nt + (lane & 7)) * c.KPB +
+                           ((lane >> 3) & 1) * 8;
+      for (int k0 = 0; k0 < 2 * N; k0 += 16) {
+        uint32_t a[4], bb[2];
+        ldsm_x4(a, pa + k0);
+        ldsm_x2(bb, pb + k0);
+        mma_bf16(acc, a, bb);
+      }
+      float* ds = Ds + ((size_t)g * c.MY + 16 * mt + (lane >> 2)) * c.MPY + 8 * nt + 2 * (lane & 3);
+      ds[0] = acc[0];
+      ds[1] = acc[1];
+      ds[8 * c.MPY] = acc[2];
+      ds[8 * c.MPY + 1] = acc[3];
+    }
+    __syncthreads();
+    for (int i = tid; i < c.G * 2 * m * m; i += kThreads) {
+      const int g = i % c.G, col = i / c.G;
+      const int kyi = col / m, kx = col - kyi * m;
+      const float* ds = Ds + (size_t)g * c.MY * c.MPY;
+      d[(long long)col * W + c0 + g] =
+          make_float2(ds[kyi * c.MPY + kx], ds[(c.KPY + kyi) * c.MPY + kx]);
+    }
+  }
+}
+
 size_t spec_smem(int N, int m) {
   const size_t m2 = 2 * m;
   return (m2 * W * W + (size_t)N * W + 3 * m2 * W + N + (size_t)N * m2) * sizeof(float2);
@@ -298,6 +467,170 @@ __global__ void __launch_bounds__(kThreads) k_spec_fwd(const float2* __restrict_
   }
   __syncthreads();
   z_idft(U, Tz, Bz + (long long)b * N * ncol * W + col * W, (long long)ncol * W, N, m);
+}
+
+// Tensor-core form of k_spec_fwd (RPM_FNO_BF16, N % 16 == 0): one block per
+// kept (ky, kx) column and all samples, in groups of 16.  Per sample, the z
+// transform to the kept kz is a BF16 product (rows Re / Im of each kz, K = 2N
+// over (z, re/im)); the channel mixing of each kz is a BF16 product over the
+// group (M = 16 samples, K = 32 over (i, re/im), N = 32 over (o, re/im), the
+// real form of the complex R[kz]); the inverse z transform is again a product
+// (rows Re / Im of each z, K over (kz, re/im)).  float32 accumulation; the
+// forward spectra V are kept in float32 for the backward pass.
+template <int N>
+struct SpecTc {
+  int m2, KPZ, MZ, KZB, KIB, MB;
+  __host__ __device__ SpecTc(int m) {
+    m2 = 2 * m;
+    KPZ = round_up(2 * m, 8);   // kz rows per part
+    MZ = 2 * KPZ;
+    KZB = 2 * N + 8;            // row stride of Az and BTa
+    KIB = 2 * KPZ + 8;          // row stride of Ainv and BTU
+    MB = 32 + 8;                // row stride of the mixing operand
+  }
+  __host__ __device__ size_t bytes() const {
+    return (size_t)2 * ((size_t)MZ * KZB + (size_t)2 * N * KIB + (size_t)W * KZB +
+                        (size_t)KPZ * 16 * MB + (size_t)16 * W * KIB) +
+           (size_t)4 * ((size_t)MZ * 16 + (size_t)2 * N * 16);
+  }
+};
+template <int N>
+size_t spec_tc_smem(int m) { return SpecTc<N>(m).bytes(); }
+
+template <int N>
+__global__ void __launch_bounds__(kThreads, 2) k_spec_fwd_tc(const float2* __restrict__ A2,
+                                                          const float2* __restrict__ R,
+                                                          float2* __restrict__ Vs,
+                                                          float2* __restrict__ Bz,
+                                                          const float2* __restrict__ twg, int m,
+                                                          int B) {
+  extern __shared__ float4 smem4[];
+  const SpecTc<N> c(m);
+  const int m2 = c.m2, ncol = 2 * m * m, col = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint16_t* Az = reinterpret_cast<uint16_t*>(smem4);       // [MZ][KZB]
+  uint16_t* Ainv = Az + (size_t)c.MZ * c.KZB;                // [2N][KIB]
+  uint16_t* BTa = Ainv + (size_t)2 * N * c.KIB;              // [W][KZB]
+  uint16_t* Vm = BTa + (size_t)W * c.KZB;                    // [KPZ][16][MB]
+  uint16_t* BTU = Vm + (size_t)c.KPZ * 16 * c.MB;            // [16][W][KIB]
+  float* Dz = reinterpret_cast<float*>(BTU + (size_t)16 * W * c.KIB);   // [MZ][16]
+  float* Di = Dz + c.MZ * 16;                                            // [2N][16]
+  const float2* Rc = R + (long long)col * m2 * W * W;
+  for (int i = tid; i < c.KPZ * N; i += kThreads) {
+    const int r = i / N, z = i - r * N;
+    float tr = 0.f, ti = 0.f;
+    if (r < m2) {
+      const float2 t = twg[(kfreq(r, m, N) * z) % N];
+      tr = t.x;
+      ti = t.y;
+    }
+    *reinterpret_cast<uint32_t*>(Az + (size_t)r * c.KZB + 2 * z) = bf16x2_bits(tr, -ti);
+    *reinterpret_cast<uint32_t*>(Az + (size_t)(c.KPZ + r) * c.KZB + 2 * z) = bf16x2_bits(ti, tr);
+    // inverse: row z (re) (Tr, Ti), row N + z (im) (-Ti, Tr) at column pair r
+    *reinterpret_cast<uint32_t*>(Ainv + (size_t)z * c.KIB + 2 * r) = bf16x2_bits(tr, ti);
+    *reinterpret_cast<uint32_t*>(Ainv + (size_t)(N + z) * c.KIB + 2 * r) = bf16x2_bits(-ti, tr);
+  }
+  const int zmt = c.MZ / 16, imt = 2 * N / 16;
+  for (int g0 = 0; g0 < B; g0 += 16) {
+    const int gb = min(16, B - g0);
+    __syncthreads();   // tables written; the previous group's readers are done
+    for (int i = tid; i < c.KPZ * 16 * c.MB / 2; i += kThreads)
+      reinterpret_cast<uint32_t*>(Vm)[i] = 0u;
+    for (int i = tid; i < 16 * W * c.KIB / 2; i += kThreads)
+      reinterpret_cast<uint32_t*>(BTU)[i] = 0u;
+    for (int bi = 0; bi < gb; ++bi) {
+      const int b = g0 + bi;
+      __syncthreads();   // BTa / Dz readers of the previous sample are done
+      for (int i = tid; i < N * W; i += kThreads) {
+        const int z = i / W, cc = i - z * W;
+        const float2 a = A2[((long long)b * N + z) * ncol * W + col * W + cc];
+        *reinterpret_cast<uint32_t*>(BTa + (size_t)cc * c.KZB + 2 * z) = bf16x2_bits(a.x, a.y);
+      }
+      __syncthreads();
+      for (int tile = warp; tile < zmt * 2; tile += kThreads / 32) {
+        const int mt = tile >> 1, nt = tile & 1;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        const uint16_t* pa = Az + (size_t)(16 * mt + (lane & 15)) * c.KZB + (lane >> 4) * 8;
+        const uint16_t* pb = BTa + (size_t)(8 * nt + (lane & 7)) * c.KZB + ((lane >> 3) & 1) * 8;
+        for (int k0 = 0; k0 < 2 * N; k0 += 16) {
+          uint32_t a[4], bb[2];
+          ldsm_x4(a, pa + k0);
+          ldsm_x2(bb, pb + k0);
+          mma_bf16(acc, a, bb);
+        }
+        float* d = Dz + (16 * mt + (lane >> 2)) * 16 + 8 * nt + 2 * (lane & 3);
+        d[0] = acc[0];
+        d[1] = acc[1];
+        d[8 * 16] = acc[2];
+        d[8 * 16 + 1] = acc[3];
+      }
+      __syncthreads();
+      float2* vs = Vs + ((long long)col * B + b) * m2 * W;
+      for (int o = tid; o < m2 * W; o += kThreads) {
+        const int kzi = o / W, cc = o - kzi * W;
+        const float re = Dz[kzi * 16 + cc], im = Dz[(c.KPZ + kzi) * 16 + cc];
+        vs[o] = make_float2(re, im);
+        *reinterpret_cast<uint32_t*>(Vm + ((size_t)kzi * 16 + bi) * c.MB + 2 * cc) =
+            bf16x2_bits(re, im);
+      }
+    }
+    __syncthreads();
+    // channel mixing per kz: U[b][(o, re/im)] = sum_(i, re/im) V[b][(i, re/im)] Rr[kz]
+    for (int tile = warp; tile < m2 * 4; tile += kThreads / 32) {
+      const int kzi = tile >> 2, nt = tile & 3;
+      const float2* rk = Rc + (size_t)kzi * W * W;
+      const int o = 4 * nt + ((lane >> 2) >> 1), ro = (lane >> 2) & 1;
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      const uint16_t* pa = Vm + ((size_t)kzi * 16 + (lane & 15)) * c.MB + (lane >> 4) * 8;
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {
+        uint32_t a[4], bb[2];
+        ldsm_x4(a, pa + 16 * ks);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int i = 8 * ks + (lane & 3) + 4 * h;
+          const float2 r = rk[i * W + o];
+          bb[h] = ro ? bf16x2_bits(r.y, r.x) : bf16x2_bits(r.x, -r.y);
+        }
+        mma_bf16(acc, a, bb);
+      }
+      // rows b = lane/4 (+8), columns n = 8 nt + 2t (+1) = (o', re/im), o' = 4 nt + t
+      const int oo = 4 * nt + (lane & 3);
+      const int b0 = lane >> 2;
+      *reinterpret_cast<uint32_t*>(BTU + ((size_t)b0 * W + oo) * c.KIB + 2 * kzi) =
+          bf16x2_bits(acc[0], acc[1]);
+      *reinterpret_cast<uint32_t*>(BTU + ((size_t)(b0 + 8) * W + oo) * c.KIB + 2 * kzi) =
+          bf16x2_bits(acc[2], acc[3]);
+    }
+    for (int bi = 0; bi < gb; ++bi) {
+      const int b = g0 + bi;
+      __syncthreads();   // BTU complete; Di readers of the previous sample are done
+      for (int tile = warp; tile < imt * 2; tile += kThreads / 32) {
+        const int mt = tile >> 1, nt = tile & 1;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        const uint16_t* pa = Ainv + (size_t)(16 * mt + (lane & 15)) * c.KIB + (lane >> 4) * 8;
+        const uint16_t* pb = BTU + ((size_t)bi * W + 8 * nt + (lane & 7)) * c.KIB +
+                             ((lane >> 3) & 1) * 8;
+        for (int k0 = 0; k0 < 2 * c.KPZ; k0 += 16) {
+          uint32_t a[4], bb[2];
+          ldsm_x4(a, pa + k0);
+          ldsm_x2(bb, pb + k0);
+          mma_bf16(acc, a, bb);
+        }
+        float* d = Di + (16 * mt + (lane >> 2)) * 16 + 8 * nt + 2 * (lane & 3);
+        d[0] = acc[0];
+        d[1] = acc[1];
+        d[8 * 16] = acc[2];
+        d[8 * 16 + 1] = acc[3];
+      }
+      __syncthreads();
+      float2* bz = Bz + (long long)b * N * ncol * W + col * W;
+      for (int i = tid; i < N * W; i += kThreads) {
+        const int z = i / W, oc = i - z * W;
+        bz[(long long)z * ncol * W + oc] = make_float2(Di[z * 16 + oc], Di[(N + z) * 16 + oc]);
+      }
+    }
+  }
 }
 
 // Backward of k_spec_fwd.  A2 holds the xy transform of dz; dU = w(kx) / N^3 *
@@ -516,6 +849,194 @@ __global__ void __launch_bounds__(kThreads, 2) k_inv_xy(const float2* __restrict
     const long long vox0 = ((long long)z * N + y0 + yy) * N + x;
     inv_pointwise<BWD>(u0, u1, Al, vin, zsave, vout, (long long)b * W * N3 + vox0,
                        (long long)b * W * N3 + vox0 + half, N3, last);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core form of k_inv_xy (RPM_FNO_BF16, N % 16 == 0).  Both inverse
+// stages are BF16 matrix products with float32 accumulation:
+//   y stage  D1[r][kx W + c] = sum_{kyi, re/im} A1[r][.] S[kyi][kx][c].(re, im),
+//            rows r < YC giving Re Y[yy = r] (Ty_re, Ty_im) and rows YC + yy
+//            giving Im Y (-Ty_im, Ty_re): M = 2 YC, K = round16(4m), Nout = m W
+//   x stage  u[yy W + c][x] = sum_{kx, re/im} Y[yy][kx][c].(re, im) w(kx) (cos, -sin)
+//            M = YC W, K = round16(2m), Nout = N
+// Each warp stages the x-stage output of one row yy (16 channels x N voxels)
+// in its own shared-memory slab and runs the pointwise end of the layer on
+// those voxels (inv_pointwise, as in k_inv_xy).
+// ---------------------------------------------------------------------------
+struct InvTc {
+  int K1, K1P, N1, M1, K2, K2P, UP, YC;
+  __host__ __device__ InvTc(int N, int m, int yc) {
+    YC = yc;
+    K1 = round_up(4 * m, 16);
+    K1P = K1 + 8;
+    N1 = m * W;
+    M1 = 2 * yc;
+    K2 = round_up(2 * m, 16);
+    K2P = K2 + 8;
+    UP = N + 4;
+  }
+  __host__ __device__ size_t bytes(int N) const {
+    return (size_t)2 * ((size_t)N1 * K1P + (size_t)M1 * K1P + (size_t)YC * W * K2P +
+                        (size_t)N * K2P) +
+           (size_t)4 * (8 * W * UP + kLayerHead);
+  }
+};
+size_t inv_tc_smem(int N, int m, int YC) { return InvTc(N, m, YC).bytes(N); }
+
+template <bool BWD, int N>
+__global__ void __launch_bounds__(kThreads, 2) k_inv_xy_tc(const float2* __restrict__ Bz,
+                                                        const float2* __restrict__ twg,
+                                                        const float* __restrict__ layer,
+                                                        const float* __restrict__ vin,
+                                                        float* __restrict__ zsave,
+                                                        float* __restrict__ vout, int m,
+                                                        int YC, int last, float inv_n3) {
+  extern __shared__ float4 smem4[];
+  const InvTc c(N, m, YC);
+  const int ncol = 2 * m * m, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint16_t* BT1 = reinterpret_cast<uint16_t*>(smem4);      // [N1][K1P]
+  uint16_t* A1 = BT1 + (size_t)c.N1 * c.K1P;                 // [M1][K1P]
+  uint16_t* A2 = A1 + (size_t)c.M1 * c.K1P;                  // [YC W][K2P]
+  uint16_t* BT2 = A2 + (size_t)YC * W * c.K2P;               // [N][K2P]
+  float* Uw = reinterpret_cast<float*>(BT2 + (size_t)N * c.K2P);   // [8][W][UP]
+  float* Al = Uw + 8 * W * c.UP;
+  const int y0 = blockIdx.x * YC, z = blockIdx.y, b = blockIdx.z;
+  const long long N3 = (long long)N * N * N;
+  const float2* src = Bz + ((long long)b * N + z) * ncol * W;
+  for (int i = tid; i < ncol * W; i += kThreads) {
+    const int cc = i % W, col = i / W;
+    const int kyi = col / m, kx = col - kyi * m;
+    const float2 sv = src[i];
+    *reinterpret_cast<uint32_t*>(BT1 + (size_t)(kx * W + cc) * c.K1P + 2 * kyi) =
+        bf16x2_bits(sv.x, sv.y);
+  }
+  const int pad1 = c.K1 - 4 * m;
+  for (int i = tid; i < c.N1 * pad1; i += kThreads)
+    BT1[(size_t)(i / pad1) * c.K1P + 4 * m + i % pad1] = 0;
+  for (int i = tid; i < YC * (c.K1 / 2); i += kThreads) {
+    const int yy = i / (c.K1 / 2), kyi = i - yy * (c.K1 / 2);
+    float tr = 0.f, ti = 0.f;
+    if (kyi < 2 * m) {
+      const float2 t = twg[(kfreq(kyi, m, N) * (y0 + yy)) % N];
+      tr = t.x;
+      ti = t.y;
+    }
+    *reinterpret_cast<uint32_t*>(A1 + (size_t)yy * c.K1P + 2 * kyi) = bf16x2_bits(tr, ti);
+    *reinterpret_cast<uint32_t*>(A1 + (size_t)(YC + yy) * c.K1P + 2 * kyi) = bf16x2_bits(-ti, tr);
+  }
+  const int pad2 = c.K2 - 2 * m;
+  for (int i = tid; i < YC * W * pad2; i += kThreads)
+    A2[(size_t)(i / pad2) * c.K2P + 2 * m + i % pad2] = 0;
+  for (int i = tid; i < N * (c.K2 / 2); i += kThreads) {
+    const int x = i / (c.K2 / 2), kx = i - x * (c.K2 / 2);
+    float wr = 0.f, wi = 0.f;
+    if (kx < m) {
+      const float w = BWD ? 1.f : (kx == 0 ? inv_n3 : 2.f * inv_n3);
+      const float2 t = twg[(kx * x) % N];
+      wr = w * t.x;
+      wi = w * t.y;
+    }
+    *reinterpret_cast<uint32_t*>(BT2 + (size_t)x * c.K2P + 2 * kx) = bf16x2_bits(wr, wi);
+  }
+  if (!BWD)
+    for (int i = tid; i < kLayerHead; i += kThreads) Al[i] = layer[i];
+  __syncthreads();
+  const int nt1 = c.N1 / 8, mt1 = c.M1 / 16;
+  for (int tile = warp; tile < mt1 * nt1; tile += kThreads / 32) {
+    const int mt = tile / nt1, nt = tile - mt * nt1;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const uint16_t* pa = A1 + (size_t)(16 * mt + (lane & 15)) * c.K1P + (lane >> 4) * 8;
+    const uint16_t* pb = BT1 + (size_t)(8 * nt + (lane & 7)) * c.K1P + ((lane >> 3) & 1) * 8;
+    for (int k0 = 0; k0 < c.K1; k0 += 16) {
+      uint32_t a[4], bb[2];
+      ldsm_x4(a, pa + k0);
+      ldsm_x2(bb, pb + k0);
+      mma_bf16(acc, a, bb);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = 16 * mt + (lane >> 2) + 8 * h;
+      const int part = r >= YC ? 1 : 0, yy = r - part * YC;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int n = 8 * nt + 2 * (lane & 3) + j;
+        const int kx = n / W, cc = n - kx * W;
+        A2[(size_t)(yy * W + cc) * c.K2P + 2 * kx + part] = bf16_bits(acc[2 * h + j]);
+      }
+    }
+  }
+  __syncthreads();
+  float* uw = Uw + (size_t)warp * W * c.UP;
+  const int half = N / 2;
+  for (int mt = warp; mt < YC; mt += kThreads / 32) {   // one row yy = mt: its 16 channels
+    for (int nt = 0; nt < N / 8; ++nt) {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      const uint16_t* pa = A2 + (size_t)(16 * mt + (lane & 15)) * c.K2P + (lane >> 4) * 8;
+      const uint16_t* pb = BT2 + (size_t)(8 * nt + (lane & 7)) * c.K2P + ((lane >> 3) & 1) * 8;
+      for (int k0 = 0; k0 < c.K2; k0 += 16) {
+        uint32_t a[4], bb[2];
+        ldsm_x4(a, pa + k0);
+        ldsm_x2(bb, pb + k0);
+        mma_bf16(acc, a, bb);
+      }
+      float* u = uw + (lane >> 2) * c.UP + 8 * nt + 2 * (lane & 3);
+      u[0] = acc[0];
+      u[1] = acc[1];
+      u[8 * c.UP] = acc[2];
+      u[8 * c.UP + 1] = acc[3];
+    }
+    __syncwarp();
+#pragma unroll 1
+    for (int x = lane; x < half; x += 32) {
+      const long long at0 = (long long)b * W * N3 + ((long long)z * N + y0 + mt) * N + x;
+      const long long at1 = at0 + half;
+      const float* u0 = uw + x;
+      const float* u1 = uw + x + half;
+      if constexpr (BWD) {
+        float g0[W], g1[W];
+#pragma unroll
+        for (int cc = 0; cc < W; ++cc) {
+          g0[cc] = vout[at0 + cc * N3];
+          g1[cc] = vout[at1 + cc * N3];
+        }
+#pragma unroll
+        for (int cc = 0; cc < W; ++cc) {
+          vout[at0 + cc * N3] = g0[cc] + u0[cc * c.UP];
+          vout[at1 + cc * N3] = g1[cc] + u1[cc * c.UP];
+        }
+      } else {   // z = A v + a + u, then the activation (as inv_pointwise)
+        float v0[W], v1[W];
+#pragma unroll
+        for (int cc = 0; cc < W; ++cc) {
+          v0[cc] = vin[at0 + cc * N3];
+          v1[cc] = vin[at1 + cc * N3];
+        }
+#pragma unroll 4
+        for (int oc = 0; oc < W; ++oc) {
+          float s0 = Al[W * W + oc] + u0[oc * c.UP], s1 = Al[W * W + oc] + u1[oc * c.UP];
+          const float4* ar = reinterpret_cast<const float4*>(Al + oc * W);
+#pragma unroll
+          for (int q = 0; q < W / 4; ++q) {
+            const float4 av = ar[q];
+            s0 = fmaf(av.x, v0[4 * q], fmaf(av.y, v0[4 * q + 1],
+                      fmaf(av.z, v0[4 * q + 2], fmaf(av.w, v0[4 * q + 3], s0))));
+            s1 = fmaf(av.x, v1[4 * q], fmaf(av.y, v1[4 * q + 1],
+                      fmaf(av.z, v1[4 * q + 2], fmaf(av.w, v1[4 * q + 3], s1))));
+          }
+          if (last) {
+            vout[at0 + oc * N3] = s0;
+            vout[at1 + oc * N3] = s1;
+          } else {
+            zsave[at0 + oc * N3] = s0;
+            zsave[at1 + oc * N3] = s1;
+            vout[at0 + oc * N3] = gelu(s0);
+            vout[at1 + oc * N3] = gelu(s1);
+          }
+        }
+      }
+    }
+    __syncwarp();
   }
 }
 
@@ -927,6 +1448,7 @@ __global__ void k_features(const uint8_t* __restrict__ phase, const float2* __re
 
 struct rpm_fno {
   int N = 0, m = 0, L = 0, Bmax = 0, ncol = 0, YC = 8;
+  bool tc = false;            // BF16 tensor-core transforms (precision RPM_FNO_BF16, N % 16 == 0)
   long long N3 = 0;
   size_t nparam = 0;
   cudaStream_t st = nullptr;
@@ -992,6 +1514,64 @@ bool stage_E(rpm_fno* f, int B, const float* E_dir) {
              "E");
 }
 
+// Truncated forward xy transform of B samples into f->A2: the BF16
+// tensor-core kernel when the network was created with RPM_FNO_BF16.
+#define RPM_FNO_TC_SIZES(X) X(32) X(48) X(64) X(96) X(128)
+
+void launch_xy_fwd(rpm_fno* f, const float* src, int B) {
+  const int N = f->N, m = f->m;
+  if (f->tc) {
+    switch (N) {
+#define RPM_CASE(NN)                                                                        \
+  case NN:                                                                                  \
+    k_xy_fwd_tc<NN><<<dim3(N, B), kThreads, xy_tc_smem(N, m), f->st>>>(src, f->A2, f->tw, m); \
+    return;
+      RPM_FNO_TC_SIZES(RPM_CASE)
+#undef RPM_CASE
+    }
+  }
+  k_xy_fwd<<<dim3(N, B), kThreads, xy_smem(N, m), f->st>>>(src, f->A2, f->tw, N, m);
+}
+
+// Forward spectral kernel of one layer: f->A2 -> f->Bz, V saved in Vs.
+void launch_spec_fwd(rpm_fno* f, int B, const float2* R, float2* Vs) {
+  const int N = f->N, m = f->m;
+  if (f->tc) {
+    switch (N) {
+#define RPM_CASE(NN)                                                                           \
+  case NN:                                                                                     \
+    k_spec_fwd_tc<NN><<<f->ncol, kThreads, spec_tc_smem<NN>(m), f->st>>>(f->A2, R, Vs, f->Bz, \
+                                                                         f->tw, m, B);         \
+    return;
+      RPM_FNO_TC_SIZES(RPM_CASE)
+#undef RPM_CASE
+    }
+  }
+  k_spec_fwd<<<dim3(f->ncol, B), kThreads, spec_smem(N, m), f->st>>>(f->A2, R, Vs, f->Bz, f->tw,
+                                                                     N, m, B);
+}
+
+// Inverse xy transform of B samples from f->Bz (pointwise end as k_inv_xy).
+template <bool BWD>
+void launch_inv_xy(rpm_fno* f, int B, const float* layer, const float* vin, float* zsave,
+                   float* vout, int last, float inv_n3) {
+  const int N = f->N, m = f->m;
+  const dim3 grid(N / f->YC, N, B);
+  if (f->tc) {
+    switch (N) {
+#define RPM_CASE(NN)                                                                     \
+  case NN:                                                                               \
+    k_inv_xy_tc<BWD, NN><<<grid, kThreads, inv_tc_smem(N, m, f->YC), f->st>>>(          \
+        f->Bz, f->tw, layer, vin, zsave, vout, m, f->YC, last, inv_n3);                 \
+    return;
+      RPM_FNO_TC_SIZES(RPM_CASE)
+#undef RPM_CASE
+    }
+  }
+  k_inv_xy<BWD><<<grid, kThreads, inv_smem(m, f->YC), f->st>>>(f->Bz, f->tw, layer, vin, zsave,
+                                                              vout, N, m, f->YC, last, inv_n3);
+}
+
 // Forward pass; keeps v_l and z_l.  out (optional), target (optional: then the
 // head also writes dv_L into dvb(0) and its partials).
 bool run_forward(rpm_fno* f, int B, const float* feat, const float* target, float* out) {
@@ -1002,13 +1582,11 @@ bool run_forward(rpm_fno* f, int B, const float* feat, const float* target, floa
   k_lift<<<nb, kThreads, 0, f->st>>>(feat, f->params, f->v(0), f->N3, B);
   if (!fck(f, cudaGetLastError(), "lift")) return false;
   for (int l = 0; l < L; ++l) {
-    k_xy_fwd<<<dim3(N, B), kThreads, xy_smem(N, m), f->st>>>(f->v(l), f->A2, f->tw, N, m);
-    k_spec_fwd<<<dim3(f->ncol, B), kThreads, spec_smem(N, m), f->st>>>(
-        f->A2, (const float2*)(f->layer(l) + kLayerHead), f->Vsl(l), f->Bz, f->tw, N, m, B);
+    launch_xy_fwd(f, f->v(l), B);
+    launch_spec_fwd(f, B, (const float2*)(f->layer(l) + kLayerHead), f->Vsl(l));
     const int last = (l == L - 1);
-    k_inv_xy<false><<<dim3(N / f->YC, N, B), kThreads, inv_smem(m, f->YC), f->st>>>(
-        f->Bz, f->tw, f->layer(l), f->v(l), last ? nullptr : f->z(l), f->v(l + 1), N, m, f->YC,
-        last, inv_n3);
+    launch_inv_xy<false>(f, B, f->layer(l), f->v(l), last ? nullptr : f->z(l), f->v(l + 1), last,
+                         inv_n3);
     if (!fck(f, cudaGetLastError(), "layer")) return false;
   }
   const float inv_nel = 1.f / (float)(total * COUT);
@@ -1037,12 +1615,11 @@ bool run_backward(rpm_fno* f, int B, const float* feat) {
                                          f->layer(l), dz, prev, f->part, f->N3, B, last);
     k_reduce<<<reduce_blocks(kNeA), 32 * kRedWarps, 0, f->st>>>(f->part, nb, kNeA, kNeA, 0,
                                                                 f->glayer(l), nullptr);
-    k_xy_fwd<<<dim3(N, B), kThreads, xy_smem(N, m), f->st>>>(dz, f->A2, f->tw, N, m);
+    launch_xy_fwd(f, dz, B);
     k_spec_bwd<<<f->ncol, kThreads, spec_smem(N, m), f->st>>>(
         f->A2, (const float2*)(f->layer(l) + kLayerHead), f->Vsl(l),
         (float2*)(f->glayer(l) + kLayerHead), f->Bz, f->tw, N, m, B, inv_n3);
-    k_inv_xy<true><<<dim3(N / f->YC, N, B), kThreads, inv_smem(m, f->YC), f->st>>>(
-        f->Bz, f->tw, nullptr, nullptr, nullptr, prev, N, m, f->YC, 0, inv_n3);
+    launch_inv_xy<true>(f, B, nullptr, nullptr, nullptr, prev, 0, inv_n3);
     if (!fck(f, cudaGetLastError(), "layer backward")) return false;
     cur = 1 - cur;
   }
@@ -1050,6 +1627,22 @@ bool run_backward(rpm_fno* f, int B, const float* feat) {
   k_reduce<<<reduce_blocks(kNeP), 32 * kRedWarps, 0, f->st>>>(f->part, nb, kNeP, kNeP, 0,
                                                                f->grads + kOffP, nullptr);
   return fck(f, cudaGetLastError(), "lift backward");
+}
+
+// Shared-memory limits of the tensor-core kernels (per grid side: sixteen
+// rows per k_inv_xy block up to N = 64, eight above; any number of modes).
+bool set_tc_smem() {
+#define RPM_CASE(NN)                                                                         \
+  if (set_smem((const void*)k_xy_fwd_tc<NN>, xy_tc_smem(NN, kMaxModes)) != cudaSuccess ||    \
+      set_smem((const void*)k_inv_xy_tc<false, NN>,                                         \
+               inv_tc_smem(NN, kMaxModes, NN <= 64 ? 16 : 8)) != cudaSuccess ||             \
+      set_smem((const void*)k_inv_xy_tc<true, NN>,                                          \
+               inv_tc_smem(NN, kMaxModes, NN <= 64 ? 16 : 8)) != cudaSuccess ||             \
+      set_smem((const void*)k_spec_fwd_tc<NN>, spec_tc_smem<NN>(kMaxModes)) != cudaSuccess)   \
+    return false;
+  RPM_FNO_TC_SIZES(RPM_CASE)
+#undef RPM_CASE
+  return true;
 }
 
 bool valid_batch(rpm_fno* f, int B) { return f && B >= 1 && B <= f->Bmax; }
@@ -1067,6 +1660,7 @@ rpm_status rpm_fno_create(const rpm_fno_config* cfg, void* cuda_stream, rpm_fno*
   if (!cfg || !out) return RPM_ERR_INVALID_ARG;
   *out = nullptr;
   const int N = cfg->n, m = cfg->modes, L = cfg->layers, B = cfg->max_batch;
+  if (cfg->precision != RPM_FNO_FP32 && cfg->precision != RPM_FNO_BF16) return RPM_ERR_INVALID_ARG;
   if (m < 1 || m > kMaxModes || L < 1 || L > RPM_FNO_MAX_LAYERS || B < 1 ||
       B > RPM_FNO_MAX_BATCH || N < 24 ||
       N > RPM_FNO_MAX_N || N % 8 != 0 || N < 2 * m)
@@ -1081,6 +1675,7 @@ rpm_status rpm_fno_create(const rpm_fno_config* cfg, void* cuda_stream, rpm_fno*
   f->nparam = rpm_fno_param_count(m, L);
   f->st = (cudaStream_t)cuda_stream;
   f->YC = (N <= 64 && N % 16 == 0) ? 16 : 8;   // rows per k_inv_xy block (divides N)
+  f->tc = cfg->precision == RPM_FNO_BF16 && N % 16 == 0;
   auto alloc = [&](void** p, size_t b) {
     cudaError_t e = cudaMalloc(p, std::max<size_t>(b, 256));
     if (e == cudaSuccess) f->bytes += b;
@@ -1114,7 +1709,10 @@ rpm_status rpm_fno_create(const rpm_fno_config* cfg, void* cuda_stream, rpm_fno*
     const double a = -2.0 * M_PI * (double)j / (double)N;
     tw[j] = make_float2((float)std::cos(a), (float)std::sin(a));
   }
-  const size_t smax = std::max(xy_smem(N, m), std::max(spec_smem(N, m), inv_smem(m, f->YC)));
+  const size_t smax = std::max(std::max(xy_smem(N, m), xy_tc_smem(N, m)),
+                               std::max(spec_smem(N, m), std::max(inv_smem(m, f->YC),
+                                                                  inv_tc_smem(N, m, f->YC))));
+
   if (smax > 227 * 1024 ||
       cudaMemcpyAsync(f->tw, tw.data(), N * sizeof(float2), cudaMemcpyHostToDevice, f->st) !=
           cudaSuccess ||
@@ -1124,10 +1722,12 @@ rpm_status rpm_fno_create(const rpm_fno_config* cfg, void* cuda_stream, rpm_fno*
       cudaMemsetAsync(f->adam2, 0, P, f->st) != cudaSuccess ||
       // the attribute is per kernel, not per network: allow the largest configuration
       set_smem((const void*)k_xy_fwd, xy_smem(RPM_FNO_MAX_N, kMaxModes)) != cudaSuccess ||
+      !set_tc_smem() ||
       set_smem((const void*)k_spec_fwd, spec_smem(RPM_FNO_MAX_N, kMaxModes)) != cudaSuccess ||
       set_smem((const void*)k_spec_bwd, spec_smem(RPM_FNO_MAX_N, kMaxModes)) != cudaSuccess ||
       set_smem((const void*)k_inv_xy<false>, inv_smem(kMaxModes, 16)) != cudaSuccess ||
       set_smem((const void*)k_inv_xy<true>, inv_smem(kMaxModes, 16)) != cudaSuccess ||
+
       set_smem((const void*)k_head, head_smem(RPM_FNO_MAX_BATCH)) != cudaSuccess ||
       cudaStreamSynchronize(f->st) != cudaSuccess) {
     cudaGetLastError();

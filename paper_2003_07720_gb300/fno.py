@@ -21,9 +21,14 @@ COUT = 36        # localisation channels H[o][j] (channel 6 o + j)
 HEADER = 768
 
 
+RPM_FNO_FP32 = 0
+RPM_FNO_BF16 = 1
+PRECISIONS = {"fp32": RPM_FNO_FP32, "bf16": RPM_FNO_BF16}
+
+
 class rpm_fno_config(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("modes", ctypes.c_int), ("layers", ctypes.c_int),
-                ("max_batch", ctypes.c_int)]
+                ("max_batch", ctypes.c_int), ("precision", ctypes.c_int)]
 
 
 class rpm_fno_adam(ctypes.Structure):
@@ -140,10 +145,14 @@ class Fno:
     """Owning wrapper of an rpm_fno handle on grid N^3."""
 
     def __init__(self, n: int, modes: int = 12, layers: int = 4, max_batch: int = 1,
-                 stream=None):
+                 stream=None, precision: str = "bf16"):
+        """precision "bf16": the truncated DFT stages as BF16 tensor-core products
+        with float32 accumulation (grids with n % 16 == 0); "fp32": float32
+        throughout."""
         self.n, self.modes, self.layers, self.max_batch = n, modes, layers, max_batch
+        self.precision = precision
         h = ctypes.c_void_p()
-        cfg = rpm_fno_config(n, modes, layers, max_batch)
+        cfg = rpm_fno_config(n, modes, layers, max_batch, PRECISIONS[precision])
         st = lib().rpm_fno_create(ctypes.byref(cfg), rpm._stream_ptr(stream), ctypes.byref(h))
         if st != rpm.RPM_OK:
             raise FnoError(f"rpm_fno_create: {lib().rpm_status_string(st).decode()}")

@@ -19,6 +19,13 @@ pytestmark = pytest.mark.gpu
 
 OUT_TOL = 2e-4
 GRAD_TOL = 1e-3
+# BF16 tensor-core transforms (precision "bf16"): every truncated DFT stage
+# rounds its operands to bfloat16 (unit roundoff 2^-9 ~ 2e-3) and accumulates
+# in float32; a layer chains two such stages forward (and the backward two
+# more), so outputs are held to 2e-2 of their largest magnitude and gradient
+# groups to 5e-2 in relative L2.
+BF16_OUT_TOL = 2e-2
+BF16_GRAD_TOL = 5e-2
 
 
 @pytest.fixture(scope="module")
@@ -61,7 +68,7 @@ def test_forward_matches_oracle(fno, N, m, L, B):
     feat, E = _inputs(N, B, N)
     ref = fo.forward(p, feat, E.astype(np.float32).astype(np.float64), m, L)
     out = torch.empty((B, 6, N, N, N), device="cuda")
-    with fno.Fno(N, m, L, max_batch=B) as net:
+    with fno.Fno(N, m, L, max_batch=B, precision="fp32") as net:
         net.set_params(p)
         net.forward(_dev(feat), E, out)
         torch.cuda.synchronize()
@@ -78,7 +85,7 @@ def test_loss_and_every_gradient_match_oracle(fno):
     target = rng.standard_normal((B, 6, N, N, N)).astype(np.float32).astype(np.float64)
     E = E.astype(np.float32).astype(np.float64)
     loss_ref, g_ref = fo.backward(p, feat, E, target, m, L)
-    with fno.Fno(N, m, L, max_batch=B) as net:
+    with fno.Fno(N, m, L, max_batch=B, precision="fp32") as net:
         net.set_params(p)
         loss = net.loss_grad(_dev(feat), E, _dev(target))
         g1 = net.get_grads()
@@ -99,7 +106,7 @@ def test_adam_step_matches_definition(fno):
     feat, E = _inputs(N, B, 5)
     target = np.zeros((B, 6, N, N, N))
     opt = dict(lr=1e-2, beta1=0.8, beta2=0.95, eps=1e-6, weight_decay=0.1)
-    with fno.Fno(N, m, L, max_batch=B) as net:
+    with fno.Fno(N, m, L, max_batch=B, precision="fp32") as net:
         net.set_params(p)
         p0 = net.get_params().astype(np.float64)
         m1 = np.zeros_like(p0)
@@ -153,7 +160,7 @@ def test_warm_started_solve_matches_cold(fno):
     E = 0.01 * ms.strain_direction(1)
     opts = rpm.rpm_default_options(tol=1e-6, p_max=20)
     eps0 = torch.empty((6, N, N, N), device="cuda")
-    with fno.Fno(N, m, L) as net, rpm.Context(cell, opts) as ctx:
+    with fno.Fno(N, m, L, precision="fp32") as net, rpm.Context(cell, opts) as ctx:
         net.set_params(_params(m, L, 12))
         net.warm_start(ctx, E, eps0)
         mean = eps0.double().mean(dim=(1, 2, 3)).cpu().numpy()
@@ -172,7 +179,7 @@ def test_training_lowers_the_loss(fno):
     feat, E = _inputs(N, B, 13)
     # a target linear in E with a pointwise localisation: eps_o = E_o (1 + tanh f0)
     target = E[:, :, None, None, None] * (1.0 + np.tanh(feat[:, :1]))
-    with fno.Fno(N, m, L, max_batch=B) as net:
+    with fno.Fno(N, m, L, max_batch=B, precision="fp32") as net:
         net.set_params(ms.fno_params(m, L, seed=14))
         f, t = _dev(feat), _dev(target)
         l0 = net.train_step(f, E, t, lr=3e-3)
@@ -183,7 +190,7 @@ def test_training_lowers_the_loss(fno):
 
 def test_bad_arguments(fno):
     from paper_2003_07720_gb300 import rpm
-    with fno.Fno(32, 4, 1, max_batch=1) as net:
+    with fno.Fno(32, 4, 1, max_batch=1, precision="fp32") as net:
         feat = torch.zeros((2, 2, 32, 32, 32), device="cuda")
         out = torch.empty((2, 6, 32, 32, 32), device="cuda")
         with pytest.raises(fno.FnoError):
@@ -233,7 +240,7 @@ def test_trained_network_gain_is_measured(fno):
     N, m, L, B = 32, 12, 4, 8
     data = fno_train.make_dataset(N, list(range(1000, 1048)))
     assert len(data.seeds) >= 24
-    with fno.Fno(N, m, L, max_batch=B) as net:
+    with fno.Fno(N, m, L, max_batch=B, precision="fp32") as net:
         net.set_params(ms.fno_params(m, L, seed=0))
         hist = fno_train.train(net, data, epochs=30, batch=B, lr=4e-3)
         assert hist[-1] < 0.9 * hist[0], hist
@@ -259,3 +266,45 @@ def test_trained_network_gain_is_measured(fno):
     assert gains, rows
     print("F saved by the learned start per held-out cell:", gains,
           "; learned starts that did not converge (cold did):", failed)
+
+
+@pytest.mark.parametrize("N,m,L,B", [(32, 12, 4, 2), (48, 8, 2, 1), (64, 12, 4, 2), (32, 5, 1, 3)])
+def test_forward_bf16_tensor_cores_matches_oracle(fno, N, m, L, B):
+    """The BF16 tensor-core transforms against the FP64 reference network."""
+    p = _round32(_params(m, L, 300 + N))
+    feat, E = _inputs(N, B, N + 1)
+    ref = fo.forward(p, feat, E.astype(np.float32).astype(np.float64), m, L)
+    out = torch.empty((B, 6, N, N, N), device="cuda")
+    with fno.Fno(N, m, L, max_batch=B, precision="bf16") as net:
+        net.set_params(p)
+        net.forward(_dev(feat), E, out)
+        torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+    assert np.all(np.isfinite(got))
+    print(f"bf16 forward N={N} m={m} L={L}: max rel err {err:.2e}")
+    assert err < BF16_OUT_TOL, err
+
+
+def test_bf16_loss_and_gradients_match_oracle(fno):
+    N, m, L, B = 32, 6, 3, 2
+    p = _round32(_params(m, L, 7))
+    feat, E = _inputs(N, B, 3)
+    rng = np.random.Generator(np.random.PCG64(4))
+    target = rng.standard_normal((B, 6, N, N, N)).astype(np.float32).astype(np.float64)
+    E = E.astype(np.float32).astype(np.float64)
+    loss_ref, g_ref = fo.backward(p, feat, E, target, m, L)
+    with fno.Fno(N, m, L, max_batch=B, precision="bf16") as net:
+        net.set_params(p)
+        loss = net.loss_grad(_dev(feat), E, _dev(target))
+        g1 = net.get_grads()
+        net.loss_grad(_dev(feat), E, _dev(target))
+        g2 = net.get_grads()
+    assert abs(loss - loss_ref) <= 1e-3 * loss_ref
+    assert np.array_equal(g1, g2), "gradients must be deterministic"
+    g = fno.unpack_params(g1, m, L)
+    for k in g_ref:
+        a, b = g[k], g_ref[k]
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        print(f"bf16 gradient {k}: rel L2 err {rel:.2e}")
+        assert rel < BF16_GRAD_TOL, (k, rel)
