@@ -262,6 +262,11 @@ __device__ __forceinline__ void pass_b_body(const GridDev& g, float2* __restrict
                                             const GammaArgs& ga) {
   using C = PencilCfg<NZ, TT>;
   constexpr int T = C::T, NZP = C::NZP;
+  constexpr int Z1 = Split<NZ>::N1, Z2 = Split<NZ>::N2;
+  // two register steps: the first reads the spectrum and the last writes it
+  // straight from / to global memory (task q -> pencil t fastest, then
+  // component, then n2, so a half-warp covers two components' lines)
+  constexpr bool DIRECT = Z2 > 1;
   extern __shared__ float2 sm[];
   float2* B = sm;
   float2* twz = B + 6 * T * NZP;
@@ -281,7 +286,36 @@ __device__ __forceinline__ void pass_b_body(const GridDev& g, float2* __restrict
     }
     pen[threadIdx.x] = q;
   }
-  {
+  if constexpr (DIRECT) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < 6 * T * Z2; q += NT) {
+      const int t = q % T, c = (q / T) % 6, n2 = q / (6 * T);
+      const int m = m0 + t;
+      const float2* src = spec + ((size_t)c * NZ + n2) * plane + m;
+      const size_t zs = (size_t)Z2 * plane;
+      float2 v[Z1];
+#pragma unroll
+      for (int i = 0; i < Z1; ++i) v[i] = m < plane ? src[i * zs] : make_float2(0.f, 0.f);
+      RegDft<Z1, false>::run(v);
+#pragma unroll
+      for (int k1 = 1; k1 < Z1; ++k1) v[k1] = cmul(v[k1], twz[n2 * Z1 + k1]);
+      float2* p = B + (c * T + t) * NZP + n2;
+#pragma unroll
+      for (int i = 0; i < Z1; ++i) p[i * Z2] = v[i];
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < 6 * T * Z1; q += NT) {   // forward step 2 in shared memory
+      const int b = q % (6 * T), k1 = q / (6 * T);
+      float2* p = B + b * NZP + k1 * Z2;
+      float2 v[Z2];
+#pragma unroll
+      for (int i = 0; i < Z2; ++i) v[i] = p[i];
+      RegDft<Z2, false>::run(v);
+#pragma unroll
+      for (int i = 0; i < Z2; ++i) p[i] = v[i];
+    }
+    __syncthreads();
+  } else {
     constexpr int TOT = 6 * NZ * T, U = 8;
     for (int base = threadIdx.x; base < TOT; base += U * NT) {
       float2 v[U];
@@ -302,9 +336,9 @@ __device__ __forceinline__ void pass_b_body(const GridDev& g, float2* __restrict
         }
       }
     }
+    __syncthreads();
+    smem_fft<NZ, false, 6 * T, NZP, 1>(B, twz);
   }
-  __syncthreads();
-  smem_fft<NZ, false, 6 * T, NZP, 1>(B, twz);
   for (int idx = threadIdx.x; idx < T * NZ; idx += blockDim.x) {
     const int sz = idx % NZ, t = idx / NZ;
     if (m0 + t >= plane) continue;
@@ -332,11 +366,42 @@ __device__ __forceinline__ void pass_b_body(const GridDev& g, float2* __restrict
     for (int c = 0; c < 6; ++c) B[(c * T + t) * NZP + sz] = tv[c];
   }
   __syncthreads();
-  smem_fft<NZ, true, 6 * T, NZP, 1>(B, twz);
-  for (int idx = threadIdx.x; idx < 6 * NZ * T; idx += blockDim.x) {
-    const int t = idx % T, r = idx / T, z = r % NZ, c = r / NZ;
-    const int m = m0 + t;
-    if (m < plane) spec[((size_t)c * NZ + z) * plane + m] = B[(c * T + t) * NZP + z];
+  if constexpr (DIRECT) {
+    for (int q = threadIdx.x; q < 6 * T * Z1; q += NT) {   // inverse step 1 in shared memory
+      const int b = q % (6 * T), k1 = q / (6 * T);
+      float2* p = B + b * NZP + k1 * Z2;
+      float2 v[Z2];
+#pragma unroll
+      for (int i = 0; i < Z2; ++i) v[i] = p[i];
+      RegDft<Z2, true>::run(v);
+#pragma unroll
+      for (int n2 = 1; n2 < Z2; ++n2) v[n2] = cmulc(v[n2], twz[n2 * Z1 + k1]);
+#pragma unroll
+      for (int i = 0; i < Z2; ++i) p[i] = v[i];
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < 6 * T * Z2; q += NT) {   // inverse step 2 -> global
+      const int t = q % T, c = (q / T) % 6, n2 = q / (6 * T);
+      const int m = m0 + t;
+      const float2* p = B + (c * T + t) * NZP + n2;
+      float2 v[Z1];
+#pragma unroll
+      for (int i = 0; i < Z1; ++i) v[i] = p[i * Z2];
+      RegDft<Z1, true>::run(v);
+      if (m < plane) {
+        float2* dst = spec + ((size_t)c * NZ + n2) * plane + m;
+        const size_t zs = (size_t)Z2 * plane;
+#pragma unroll
+        for (int i = 0; i < Z1; ++i) dst[i * zs] = v[i];
+      }
+    }
+  } else {
+    smem_fft<NZ, true, 6 * T, NZP, 1>(B, twz);
+    for (int idx = threadIdx.x; idx < 6 * NZ * T; idx += blockDim.x) {
+      const int t = idx % T, r = idx / T, z = r % NZ, c = r / NZ;
+      const int m = m0 + t;
+      if (m < plane) spec[((size_t)c * NZ + z) * plane + m] = B[(c * T + t) * NZP + z];
+    }
   }
 }
 
@@ -1073,6 +1138,81 @@ __global__ void __launch_bounds__(kThreads) k_ypencil(GridDev g, float2* __restr
   }
 }
 
+// The y pass of the five-pass variant with its outer FFT steps on global
+// memory: the first register step reads the TY columns straight from the
+// spectrum, the second writes them straight back, and shared memory holds the
+// exchange between the two steps only (column stride NY + 1: conflict-free).
+template <int NY, bool INV>
+__global__ void __launch_bounds__(kThreads) k_ypencil_direct(GridDev g, float2* __restrict__ spec) {
+  using C = YPencilCfg<NY>;
+  constexpr int TY = C::TY, NYP = C::NYP;
+  constexpr int Y1 = Split<NY>::N1, Y2 = Split<NY>::N2;
+  static_assert(Y2 > 1, "two register steps");
+  extern __shared__ __align__(16) float2 sm[];
+  float2* B = sm;                  // [TY][NYP]
+  float2* twy = B + TY * NYP;
+  allow_dependent_launch();
+  for (int i = threadIdx.x; i < NY; i += blockDim.x) twy[i] = g.tw_y[i];
+  grid_dependency_wait();
+  __syncthreads();
+  const int sx0 = blockIdx.x * TY;
+  const int SX = g.nxh + 1;
+  float2* pl = spec + (size_t)blockIdx.y * g.plane;     // blockIdx.y = c * nz + z
+  if (!INV) {
+    for (int q = threadIdx.x; q < TY * Y2; q += blockDim.x) {   // step 1: Y1-point, stride Y2
+      const int t = q % TY, n2 = q / TY;
+      const bool ok = sx0 + t < SX;
+      float2 v[Y1];
+#pragma unroll
+      for (int i = 0; i < Y1; ++i)
+        v[i] = ok ? pl[(size_t)(n2 + Y2 * i) * SX + sx0 + t] : make_float2(0.f, 0.f);
+      RegDft<Y1, false>::run(v);
+#pragma unroll
+      for (int k1 = 1; k1 < Y1; ++k1) v[k1] = cmul(v[k1], twy[n2 * Y1 + k1]);
+#pragma unroll
+      for (int i = 0; i < Y1; ++i) B[t * NYP + n2 + Y2 * i] = v[i];
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < TY * Y1; q += blockDim.x) {   // step 2: Y2-point, contiguous
+      const int t = q % TY, k1 = q / TY;
+      float2 v[Y2];
+#pragma unroll
+      for (int i = 0; i < Y2; ++i) v[i] = B[t * NYP + k1 * Y2 + i];
+      RegDft<Y2, false>::run(v);
+      if (sx0 + t < SX) {
+#pragma unroll
+        for (int i = 0; i < Y2; ++i) pl[(size_t)(k1 * Y2 + i) * SX + sx0 + t] = v[i];
+      }
+    }
+  } else {
+    for (int q = threadIdx.x; q < TY * Y1; q += blockDim.x) {   // inverse step 1
+      const int t = q % TY, k1 = q / TY;
+      const bool ok = sx0 + t < SX;
+      float2 v[Y2];
+#pragma unroll
+      for (int i = 0; i < Y2; ++i)
+        v[i] = ok ? pl[(size_t)(k1 * Y2 + i) * SX + sx0 + t] : make_float2(0.f, 0.f);
+      RegDft<Y2, true>::run(v);
+#pragma unroll
+      for (int n2 = 1; n2 < Y2; ++n2) v[n2] = cmulc(v[n2], twy[n2 * Y1 + k1]);
+#pragma unroll
+      for (int i = 0; i < Y2; ++i) B[t * NYP + k1 * Y2 + i] = v[i];
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < TY * Y2; q += blockDim.x) {   // inverse step 2
+      const int t = q % TY, n2 = q / TY;
+      float2 v[Y1];
+#pragma unroll
+      for (int i = 0; i < Y1; ++i) v[i] = B[t * NYP + n2 + Y2 * i];
+      RegDft<Y1, true>::run(v);
+      if (sx0 + t < SX) {
+#pragma unroll
+        for (int i = 0; i < Y1; ++i) pl[(size_t)(n2 + Y2 * i) * SX + sx0 + t] = v[i];
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -1157,6 +1297,14 @@ static cudaError_t launch_ypencil(const GridDev& g, float2* spec, bool inv, cuda
   const size_t smem = (size_t)(C::TY * C::NYP + NY) * sizeof(float2);
   const dim3 grid((g.nxh + 1 + C::TY - 1) / C::TY, 6 * g.nz);
   cudaError_t e;
+  if constexpr (Split<NY>::N2 > 1) {
+    if (inv) {
+      if ((e = set_smem(k_ypencil_direct<NY, true>, smem)) != cudaSuccess) return e;
+      return launch_pdl(k_ypencil_direct<NY, true>, grid, kThreads, smem, st, g, spec);
+    }
+    if ((e = set_smem(k_ypencil_direct<NY, false>, smem)) != cudaSuccess) return e;
+    return launch_pdl(k_ypencil_direct<NY, false>, grid, kThreads, smem, st, g, spec);
+  }
   if (inv) {
     if ((e = set_smem(k_ypencil<NY, true>, smem)) != cudaSuccess) return e;
     k_ypencil<NY, true><<<grid, kThreads, smem, st>>>(g, spec);
