@@ -403,3 +403,24 @@ def test_autotuned_tile_gives_identical_solve(rpm, n):
     assert t1 in (max(t0 // 2, 1), t0, 2 * t0), (t0, t1)
     assert ia["converged"] and ib["converged"]
     assert ia["mean_stress"] == ib["mean_stress"] and ia["iters"] == ib["iters"]
+
+
+def test_batched_sweep_32_members_ceff_match_oracle(rpm):
+    """The 32^3 members of the batched effective-stiffness sweep (contrast
+    1e-2 ... 1e3) through the batch driver, every entry of C_eff against the
+    FP64 oracle's (tests/golden, solved to 1e-8) at the effective-stiffness
+    tolerance."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                    "c4_32_oracle_ceff.json")))
+    seeds = sorted(int(k) for k in g)
+    cells = [ms.cell_batch_member(s) for s in seeds]
+    opts = rpm.rpm_default_options(tol=1e-7, p_max=20, max_iters=3000)
+    C, infos, stat, st = rpm.rpm_effective_stiffness_batch(cells, opts, n_workers=4,
+                                                           raise_on_failure=False)
+    for i, s in enumerate(seeds):
+        assert stat[i] == rpm.RPM_OK, (s, stat[i])
+        ref = np.array(g[str(s)]["C_eff"])
+        err = np.max(np.abs(C[i] - ref)) / np.max(np.abs(ref))
+        assert err < CEFF_TOL, (s, g[str(s)]["contrast"], err)
