@@ -1108,6 +1108,121 @@ __global__ void __launch_bounds__(kThreads) k_rows_inv(GridDev g, const float2* 
   }
 }
 
+// The inverse x-row pass of the five-pass variant with the tangling fused
+// into x step 1 and x step 2 writing the real rows straight to global memory
+// (nx/2 with a two-step split and an even first factor).  Rows past ny are
+// skipped.  (A forward counterpart -- strain rows read in x step 1, untangling
+// fused into x step 2 -- measured slower than k_rows_fwd at 256^3: 280 against
+// 248 us.)
+template <int NX>
+__global__ void __launch_bounds__(kThreads) k_rows_inv_direct(GridDev g, const float2* __restrict__ spec,
+                                                              float* __restrict__ outp, float scale) {
+  constexpr int NXH = NX / 2, SX = NXH + 1;
+  constexpr int X1 = Split<NXH>::N1, X2 = Split<NXH>::N2;
+  static_assert(X2 > 1 && X1 % 2 == 0, "x split must have two steps and an even first factor");
+  extern __shared__ float2 sm[];
+  float2* P = sm;                                  // [SX][kRowsP]
+  float2* twx = P + SX * kRowsP;
+  float2* r2c = twx + NXH;
+  const int c = blockIdx.x, y0 = blockIdx.y * kRows, z = blockIdx.z;
+  const int ny = g.ny;
+  allow_dependent_launch();
+  for (int i = threadIdx.x; i < NXH; i += blockDim.x) twx[i] = g.tw_x[i];
+  for (int i = threadIdx.x; i < SX; i += blockDim.x) r2c[i] = g.r2c_w[i];
+  grid_dependency_wait();
+  const float2* src = spec + ((size_t)c * g.nz + z) * g.plane + (size_t)y0 * SX;
+  for (int idx = threadIdx.x; idx < kRows * SX; idx += blockDim.x) {
+    const int r = idx / SX, sx = idx - r * SX;
+    P[sx * kRowsP + r] = (y0 + r < ny) ? src[idx] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  constexpr int NU = X1 / 2 + 1;   // tangling fused into x step 1 (inverse)
+  constexpr int LS = kRowsP;
+  for (int t = threadIdx.x; t < kRows * NU; t += blockDim.x) {
+    const int b = t % kRows, u = t / kRows;
+    float2* p = P + b;
+    if (u == 0 || u == X1 / 2) {
+      const int k1 = u;
+      float2 v[X2];
+#pragma unroll
+      for (int i = 0; i < X2; ++i) v[i] = p[(k1 * X2 + i) * LS];
+      float2 o[X2];
+      if (k1 == 0) {
+        o[0] = c2r_pre(v[0], p[NXH * LS], make_float2(1.f, 0.f));
+#pragma unroll
+        for (int i = 1; i < X2; ++i) {
+          const int ip = X2 - i;
+          if (i < ip) {
+            o[i] = c2r_pre(v[i], v[ip], r2c[X1 * i]);
+            o[ip] = c2r_pre(v[ip], v[i], r2c[X1 * ip]);
+          } else if (i == ip) {
+            o[i] = c2r_pre(v[i], v[i], r2c[X1 * i]);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < X2; ++i) {
+          const int ip = X2 - 1 - i;
+          if (i < ip) {
+            o[i] = c2r_pre(v[i], v[ip], r2c[X1 / 2 + X1 * i]);
+            o[ip] = c2r_pre(v[ip], v[i], r2c[X1 / 2 + X1 * ip]);
+          } else if (i == ip) {
+            o[i] = c2r_pre(v[i], v[i], r2c[X1 / 2 + X1 * i]);
+          }
+        }
+      }
+      RegDft<X2, true>::run(o);
+#pragma unroll
+      for (int n2 = 1; n2 < X2; ++n2) o[n2] = cmulc(o[n2], twx[n2 * X1 + k1]);
+#pragma unroll
+      for (int i = 0; i < X2; ++i) p[(k1 * X2 + i) * LS] = o[i];
+    } else {
+      const int k1 = u, k1p = X1 - u;
+      float2 va[X2], vb[X2];
+#pragma unroll
+      for (int i = 0; i < X2; ++i) {
+        va[i] = p[(k1 * X2 + i) * LS];
+        vb[i] = p[(k1p * X2 + i) * LS];
+      }
+      float2 oa[X2], ob[X2];
+#pragma unroll
+      for (int i = 0; i < X2; ++i) {
+        const int ip = X2 - 1 - i;
+        oa[i] = c2r_pre(va[i], vb[ip], r2c[k1 + X1 * i]);
+        ob[ip] = c2r_pre(vb[ip], va[i], r2c[k1p + X1 * ip]);
+      }
+      RegDft<X2, true>::run(oa);
+      RegDft<X2, true>::run(ob);
+#pragma unroll
+      for (int n2 = 1; n2 < X2; ++n2) {
+        oa[n2] = cmulc(oa[n2], twx[n2 * X1 + k1]);
+        ob[n2] = cmulc(ob[n2], twx[n2 * X1 + k1p]);
+      }
+#pragma unroll
+      for (int i = 0; i < X2; ++i) {
+        p[(k1 * X2 + i) * LS] = oa[i];
+        p[(k1p * X2 + i) * LS] = ob[i];
+      }
+    }
+  }
+  __syncthreads();
+  const size_t nf2 = (size_t)g.n / 2;
+  float2* out2 = reinterpret_cast<float2*>(outp) + c * nf2 + ((size_t)z * ny + y0) * NXH;
+  for (int q = threadIdx.x; q < kRows * X2; q += blockDim.x) {   // x step 2 -> global
+    int r, n2;
+    row_task<X2, kRows>(q, r, n2);
+    float2 v[X1];
+#pragma unroll
+    for (int i = 0; i < X1; ++i) v[i] = P[(n2 + X2 * i) * kRowsP + r];
+    RegDft<X1, true>::run(v);
+    if (y0 + r < ny) {
+      float2* o = out2 + (size_t)r * NXH + n2;
+#pragma unroll
+      for (int i = 0; i < X1; ++i) o[i * X2] = cscale(v[i], scale);
+    }
+  }
+}
+
 // In-place FFT along y of TY consecutive x slots of one (component, z) plane.
 template <int NY>
 struct YPencilCfg {
@@ -1276,6 +1391,15 @@ static cudaError_t launch_rows(const GridDev& g, const float* in, float* out, fl
                                int mode, int which, cudaStream_t st) {
   constexpr int NXH = NX / 2, SX = NXH + 1;
   const dim3 grid(6, (g.ny + kRows - 1) / kRows, g.nz);
+  if constexpr (Split<NXH>::N2 > 1 && Split<NXH>::N1 % 2 == 0) {
+    if (which == 1) {
+      const size_t smem = (size_t)(SX * kRowsP + NXH + SX) * sizeof(float2);
+      cudaError_t e;
+      if ((e = set_smem(k_rows_inv_direct<NX>, smem)) != cudaSuccess) return e;
+      return launch_pdl(k_rows_inv_direct<NX>, grid, kThreads, smem, st, g, (const float2*)spec,
+                        out, 1.0f / (float)g.n);
+    }
+  }
   if (which == 0) {
     const dim3 grid_f(2, (g.ny + kRowsG - 1) / kRowsG, g.nz);
     const size_t smem = (size_t)(SX * kLinesGP + NXH + SX + 256) * sizeof(float2);
@@ -1320,24 +1444,6 @@ static cudaError_t launch_ypencil(const GridDev& g, float2* spec, bool inv, cuda
 // first factor; the fused pencil pass: 128 / split_n1(nz) pencils per block
 #define RPM_FUSED_PLANE_SIZES(X) X(48) X(64) X(96) X(128)
 #define RPM_FUSED_Z_SIZES(X) X(32) X(48) X(64) X(96) X(128)
-
-// Launch with programmatic stream serialization: the kernel may begin (its
-// fixed-table prologue) while the previous kernel of the stream finishes.
-template <typename... KArgs, typename... Args>
-static cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, int threads, size_t smem,
-                              cudaStream_t st, Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = dim3(threads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, args...);
-}
 
 template <int NX>
 static cudaError_t launch_fused_plane(const GridDev& g, const float* in, float* out, float2* spec,

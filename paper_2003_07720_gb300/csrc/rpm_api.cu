@@ -33,6 +33,7 @@ constexpr int kSums = 0;              // 1 + kPCap reduced sums
 constexpr int kC = kSums + kPCap + 8;   // Newton correction c
 constexpr int kRes = kC + kPCap;      // residual
 constexpr int kBatch = 4;             // steps between host reads while the basis is empty
+constexpr int kBatchMax = 16;         // longest batch when the decay rate predicts it
 constexpr int kFields = 10;           // field buffers of a context (see rpm_ctx::fields)
 constexpr int kMaxRebase = 16;        // re-centrings of one solve (see solve_impl)
 // Basis growth is skipped while |xi^nu - xi^(nu-1)| < kGrowNoise |xi|: such a
@@ -833,6 +834,8 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
   const double r0 = r;
   double r_best = r;
   int it_best = 0;
+  double r_prev = r;   // residual and step of the previous host read
+  int it_prev = 0;
   inf.residual0 = r0;
   rpm_status status = RPM_OK;
   for (;;) {
@@ -852,9 +855,20 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
     int batch = 1;
     if (c->p == 0 || (r > 1e2 * o.tol && !c->trace_res)) {
       batch = kBatch;
+      // Predictive batching: with the residual falling geometrically at the
+      // rate seen since the last read, a batch ends before the step that
+      // would meet tol, so no step runs past it (one host read per batch).
+      if (!c->trace_res && it > it_prev && r_prev > r && r > o.tol) {
+        const double rate = std::pow(r / r_prev, 1.0 / (double)(it - it_prev));
+        const double to_tol = std::log(o.tol / r) / std::log(rate);
+        if (std::isfinite(to_tol) && to_tol > 1.0)
+          batch = std::max(batch, std::min(kBatchMax, (int)(0.8 * to_tol)));
+      }
       if (c->p < std::min(o.p_max, c->p_cap)) batch = std::min(batch, o.n_max + 1 - nu);
       batch = std::max(1, std::min(batch, o.max_iters - it));
     }
+    r_prev = r;
+    it_prev = it;
     for (int b = 0; b < batch; ++b) {
       float* eps_next;
       if (c->p == 0) {
