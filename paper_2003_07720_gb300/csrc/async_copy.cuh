@@ -1,5 +1,6 @@
 // Bulk asynchronous copies between global and shared memory (sm_90+ PTX,
-// used here on sm_103a) and the shared-memory barriers that track them.
+// used here on sm_103a), the shared-memory barriers that track them, and
+// the cluster barrier and distributed-shared-memory loads.
 //
 //   bulk_load   global -> shared, completion counted in bytes on an mbarrier
 //   bulk_store  shared -> global, tracked by bulk groups of the issuing thread
@@ -113,22 +114,60 @@ __device__ __forceinline__ void allow_dependent_launch() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Thread-block clusters.  cluster_sync: every thread of every block of the
+// cluster arrives (release) and waits (acquire), so shared-memory writes
+// before it are visible to the other blocks after it; all threads of a block
+// must execute it.  cluster_map: the address of `p` in the shared memory of
+// the cluster's block `rank`; ld_cluster_f2 reads through such an address.
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile(
+      "barrier.cluster.arrive.release.aligned;\n\t"
+      "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_map(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_addr(p)), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ float2 ld_cluster_f2(uint32_t addr) {
+  float2 v;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+  return v;
+}
+
 // Launch with programmatic stream serialization: the kernel may begin (its
 // fixed-table prologue) while the previous kernel of the stream finishes.
+// cluster > 1 groups that many consecutive blocks (along x) into a cluster.
 template <typename... KArgs, typename... Args>
-inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, int threads, size_t smem,
-                              cudaStream_t st, Args... args) {
+inline cudaError_t launch_pdl_cluster(void (*kernel)(KArgs...), dim3 grid, int threads,
+                                      size_t smem, cudaStream_t st, unsigned cluster,
+                                      Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = dim3(threads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  if (cluster > 1) {
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = cluster;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
+    cfg.numAttrs = 2;
+  }
   return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, int threads, size_t smem,
+                              cudaStream_t st, Args... args) {
+  return launch_pdl_cluster(kernel, grid, threads, smem, st, 1u, args...);
 }
 
 }  // namespace rpm

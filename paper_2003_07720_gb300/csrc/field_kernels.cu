@@ -407,7 +407,8 @@ cudaError_t launch_axpby(float* out, float a, const float* x, float b, const flo
 
 // eps_next = (C + C0)^-1 : (s_a + C0 : eps_b), Algorithm 3, per voxel; the
 // inverse of an isotropic stiffness (lam_s, mu_s) maps t to
-// (t - lam_s / (3 lam_s + 2 mu_s) tr(t) I) / (2 mu_s).
+// (t - k_s tr(t) I) h_s with k_s = lam_s / (3 lam_s + 2 mu_s), h_s = 1 / (2 mu_s),
+// both precomputed per phase in the table (lam_a, mu_a, k_s, h_s).
 __global__ void __launch_bounds__(kRedThreads) k_pol_post(const float4* __restrict__ eps,
                                                           const float4* __restrict__ epsb,
                                                           const uchar4* __restrict__ phase,
@@ -436,9 +437,7 @@ __global__ void __launch_bounds__(kRedThreads) k_pol_post(const float4* __restri
 #pragma unroll
       for (int c = 0; c < 3; ++c) t[c] += pm[k].x * tre + lam0 * trb;
       const float trt = t[0] + t[1] + t[2];
-      const float lam_s = pm[k].z, mu_s = pm[k].w;
-      const float sh = lam_s / (3.f * lam_s + 2.f * mu_s) * trt;
-      const float inv2mu = 0.5f / mu_s;
+      const float sh = pm[k].z * trt, inv2mu = pm[k].w;
 #pragma unroll
       for (int c = 0; c < 6; ++c) o[c][k] = (t[c] - (c < 3 ? sh : 0.f)) * inv2mu;
     }

@@ -631,15 +631,47 @@ __global__ void __launch_bounds__(kPlaneThreads, Split<NX / 2>::N1 >= 16 ? 2 : k
   }
 }
 
+// Algorithm 3's last step at one voxel: out = (C + C0)^-1 : (s_a + C0 : eps_b)
+// with s_a = lam_a tr(eps) I + 2 mu_a eps and (C + C0) = (lam_s, mu_s); the
+// inverse of an isotropic stiffness maps t to (t - k_s tr(t) I) h_s with
+// k_s = lam_s / (3 lam_s + 2 mu_s), h_s = 1 / (2 mu_s).  pm = (lam_a, mu_a,
+// k_s, h_s) of the voxel's phase.
+__device__ __forceinline__ void post_normal(const float e[3], const float b[3], float4 pm,
+                                            float lam0, float mu0, float o[3]) {
+  const float tre = e[0] + e[1] + e[2];
+  const float trb = b[0] + b[1] + b[2];
+  float t[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    t[k] = 2.f * pm.y * e[k] + 2.f * mu0 * b[k];
+    t[k] += pm.x * tre + lam0 * trb;
+  }
+  const float sh = pm.z * (t[0] + t[1] + t[2]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) o[k] = (t[k] - sh) * pm.w;
+}
+
+__device__ __forceinline__ float post_shear(float e, float b, float4 pm, float mu0) {
+  return (2.f * pm.y * e + 2.f * mu0 * b) * pm.w;
+}
+
 // Pass C, one block per (component, z).  The spectrum plane arrives by one
 // bulk asynchronous copy; y step 1 packs the DC and Nyquist x columns as
 // X_0 + i X_nx/2 (their inverse y transforms are real, so the result holds
 // both in its real and imaginary parts); the tangling is fused into x step
 // 1; x step 2 writes the real rows to global memory, scaled.
-template <int NX, int NY>
+//
+// POST: the pass ends with Algorithm 3's post-step instead (Section 5.5),
+// the transformed planes being eps_b and `eps` the map's input.  Blocks are
+// numbered z * 6 + c and run in clusters of three: the shear blocks apply
+// the post-step to their own component on the way out; the three normal
+// blocks of a plane, which need tr(eps_b), keep their real planes in shared
+// memory and each finishes all three normal components on a third of the
+// plane, reading the other two planes from the cluster's shared memory.
+template <int NX, int NY, bool POST>
 __global__ void __launch_bounds__(kPlaneThreads, kPlaneMinBlocks)
     k_plane_inv(GridDev g, const float2* __restrict__ spec, float* __restrict__ outp,
-                float scale) {
+                float scale, const float* __restrict__ eps, const float4* __restrict__ post) {
   constexpr int NXH = NX / 2, SX = NXH + 1, PL = NY * SX;
   constexpr int X1 = Split<NXH>::N1, X2 = Split<NXH>::N2;
   constexpr int Y1 = Split<NY>::N1, Y2 = Split<NY>::N2;
@@ -650,9 +682,13 @@ __global__ void __launch_bounds__(kPlaneThreads, kPlaneMinBlocks)
   float2* twx = P + PL;
   float2* twy = twx + NXH;
   float2* r2c = twy + NY;
+  float4* pt = reinterpret_cast<float4*>(r2c + SX + ((PL + NXH + NY + SX) & 1));   // POST
   __shared__ __align__(8) uint64_t bar;
   __shared__ int fail;
-  const int item = blockIdx.x;   // c * nz + z
+  const int c = POST ? (int)blockIdx.x % 6 : (int)blockIdx.x / g.nz;
+  const int z = POST ? (int)blockIdx.x / 6 : (int)blockIdx.x - c * g.nz;
+  const int item = c * g.nz + z;
+  const bool gather = POST && c < 3;   // a normal block of a post-step cluster
   allow_dependent_launch();
   if (threadIdx.x == 0) {
     fail = 0;
@@ -662,6 +698,8 @@ __global__ void __launch_bounds__(kPlaneThreads, kPlaneMinBlocks)
   for (int i = threadIdx.x; i < NXH; i += blockDim.x) twx[i] = g.tw_x[i];
   for (int i = threadIdx.x; i < NY; i += blockDim.x) twy[i] = g.tw_y[i];
   for (int i = threadIdx.x; i < SX; i += blockDim.x) r2c[i] = g.r2c_w[i];
+  if (POST)
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) pt[i] = post[i];
   grid_dependency_wait();
   if (threadIdx.x == 0) {
     mbar_arrive_expect_tx(&bar, PL * 8);
@@ -674,6 +712,10 @@ __global__ void __launch_bounds__(kPlaneThreads, kPlaneMinBlocks)
     if (threadIdx.x == 0) {
       atomicExch(g.err, 1);
       mbar_wait(&bar, 0);
+    }
+    if (gather) {   // the cluster's two barriers are still met
+      cluster_sync();
+      cluster_sync();
     }
     return;
   }
@@ -777,20 +819,90 @@ __global__ void __launch_bounds__(kPlaneThreads, kPlaneMinBlocks)
     }
   }
   __syncthreads();
-  const int c = item / g.nz, z = item - c * g.nz;
-  float2* out2 = reinterpret_cast<float2*>(outp) + (size_t)c * (g.n / 2) + (size_t)z * NY * NXH;
-  for (int q = threadIdx.x; q < NY * X2; q += blockDim.x) {   // x step 2 (inverse) -> global
+  const size_t nf2 = (size_t)g.n / 2, zoff = (size_t)z * NY * NXH;
+  float2* out2 = reinterpret_cast<float2*>(outp) + zoff;
+  const float2* e2 = reinterpret_cast<const float2*>(eps) + zoff;
+  const uchar2* ph2 = reinterpret_cast<const uchar2*>(g.phase) + zoff;
+  for (int q = threadIdx.x; q < NY * X2; q += blockDim.x) {   // x step 2 (inverse)
     int y, n2;
     row_task<X2, NY>(q, y, n2);
-    const float2* p = P + y * SX + n2;
+    float2* p = P + y * SX + n2;
+    const int r = y * NXH + n2;
+    float2 ev[X1];   // shear post-step: the map's input and phases, loaded ahead
+    uchar2 pv[X1];   // of the transform where the registers allow
+    constexpr bool AHEAD = X1 <= 8;
+    if (POST && AHEAD && !gather) {
+#pragma unroll
+      for (int i = 0; i < X1; ++i) {
+        ev[i] = e2[c * nf2 + r + i * X2];
+        pv[i] = ph2[r + i * X2];
+      }
+    }
     float2 v[X1];
 #pragma unroll
     for (int i = 0; i < X1; ++i) v[i] = p[i * X2];
     RegDft<X1, true>::run(v);
-    float2* o = out2 + y * NXH + n2;
+    if (!POST) {   // -> global
 #pragma unroll
-    for (int i = 0; i < X1; ++i) o[i * X2] = cscale(v[i], scale);
+      for (int i = 0; i < X1; ++i) out2[c * nf2 + r + i * X2] = cscale(v[i], scale);
+    } else if (gather) {   // -> the block's own slots, for the cluster's post-step
+#pragma unroll
+      for (int i = 0; i < X1; ++i) p[i * X2] = cscale(v[i], scale);
+    } else {   // shear component: post-step on the way out
+#pragma unroll
+      for (int i = 0; i < X1; ++i) {
+        if (!AHEAD) {
+          ev[i] = e2[c * nf2 + r + i * X2];
+          pv[i] = ph2[r + i * X2];
+        }
+        const float2 b = cscale(v[i], scale);
+        out2[c * nf2 + r + i * X2] = make_float2(post_shear(ev[i].x, b.x, pt[pv[i].x], g.mu0),
+                                                 post_shear(ev[i].y, b.y, pt[pv[i].y], g.mu0));
+      }
+    }
   }
+  if (!gather) return;
+  // eps_b of the three normal components sits in the cluster's blocks 0, 1, 2
+  // (rank = c), at slot y * SX + h for the float2 pair h of row y.  Each
+  // thread takes U float2 pairs at a time, all loads issued before any use.
+  cluster_sync();
+  uint32_t rb[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) rb[k] = cluster_map(P, (uint32_t)k);
+  constexpr int U = 4, STRIDE = 3 * kPlaneThreads, TOT = NY * NXH;
+  for (int f0 = threadIdx.x + c * kPlaneThreads; f0 < TOT; f0 += U * STRIDE) {
+    float2 b[U][3], e[U][3];
+    uchar2 ph[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int f = f0 + u * STRIDE;
+      if (f < TOT) {
+        const int s = f + f / NXH;   // y * SX + h
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          b[u][k] = ld_cluster_f2(rb[k] + 8u * (uint32_t)s);
+          e[u][k] = e2[k * nf2 + f];
+        }
+        ph[u] = ph2[f];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int f = f0 + u * STRIDE;
+      if (f < TOT) {
+        const float ex[3] = {e[u][0].x, e[u][1].x, e[u][2].x};
+        const float ey[3] = {e[u][0].y, e[u][1].y, e[u][2].y};
+        const float bx[3] = {b[u][0].x, b[u][1].x, b[u][2].x};
+        const float by[3] = {b[u][0].y, b[u][1].y, b[u][2].y};
+        float ox[3], oy[3];
+        post_normal(ex, bx, pt[ph[u].x], g.lam0, g.mu0, ox);
+        post_normal(ey, by, pt[ph[u].y], g.lam0, g.mu0, oy);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) out2[k * nf2 + f] = make_float2(ox[k], oy[k]);
+      }
+    }
+  }
+  cluster_sync();   // no block leaves while another still reads its planes
 }
 
 // Pass B with T = 128 / split_n1(nz) pencils per block and 256 threads.
@@ -1457,9 +1569,23 @@ static cudaError_t launch_fused_plane(const GridDev& g, const float* in, float* 
     return launch_pdl(k_plane_fwd<NX, NX>, dim3(6, g.nz), kPlaneThreads,
                       smem + 256 * sizeof(float2), st, g, in, spec, mode);
   }
-  if ((e = set_smem(k_plane_inv<NX, NX>, smem)) != cudaSuccess) return e;
-  return launch_pdl(k_plane_inv<NX, NX>, dim3(6 * g.nz), kPlaneThreads, smem, st, g,
-                    (const float2*)spec, out, 1.0f / (float)g.n);
+  if ((e = set_smem(k_plane_inv<NX, NX, false>, smem)) != cudaSuccess) return e;
+  return launch_pdl(k_plane_inv<NX, NX, false>, dim3(6 * g.nz), kPlaneThreads, smem, st, g,
+                    (const float2*)spec, out, 1.0f / (float)g.n, (const float*)nullptr,
+                    (const float4*)nullptr);
+}
+
+// pass C with Algorithm 3's post-step (clusters of three blocks)
+template <int NX>
+static cudaError_t launch_fused_inv_post(const GridDev& g, float* out, float2* spec,
+                                         const float* eps, const float4* post, cudaStream_t st) {
+  constexpr int NXH = NX / 2, SX = NXH + 1;
+  constexpr int F2 = NX * SX + NXH + NX + SX;
+  const size_t smem = (size_t)(F2 + (F2 & 1)) * sizeof(float2) + 256 * sizeof(float4);
+  cudaError_t e;
+  if ((e = set_smem(k_plane_inv<NX, NX, true>, smem)) != cudaSuccess) return e;
+  return launch_pdl_cluster(k_plane_inv<NX, NX, true>, dim3(6 * g.nz), kPlaneThreads, smem, st,
+                            3u, g, (const float2*)spec, out, 1.0f / (float)g.n, eps, post);
 }
 
 template <int NZ>
@@ -1499,6 +1625,17 @@ static cudaError_t dispatch_fused_plane(const GridDev& g, const float* in, float
   switch (g.nx) {
 #define RPM_CASE(N) \
   case N: return launch_fused_plane<N>(g, in, out, spec, mode, which, st);
+    RPM_FUSED_PLANE_SIZES(RPM_CASE)
+#undef RPM_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+static cudaError_t dispatch_fused_inv_post(const GridDev& g, float* out, float2* spec,
+                                           const float* eps, const float4* post, cudaStream_t st) {
+  switch (g.nx) {
+#define RPM_CASE(N) \
+  case N: return launch_fused_inv_post<N>(g, out, spec, eps, post, st);
     RPM_FUSED_PLANE_SIZES(RPM_CASE)
 #undef RPM_CASE
     default: return cudaErrorInvalidValue;
@@ -1608,18 +1745,51 @@ bool grid_supported(int nx, int ny, int nz) {
   return xy_size_ok(nx) && xy_size_ok(ny) && z_size_ok(nz);
 }
 
-cudaError_t launch_apply_gamma(const GridDev& g, const float* in, float* out, float2* spec,
-                               const double E[6], int mode, cudaStream_t st) {
+static GammaArgs gamma_args(const GridDev& g, const double E[6]) {
   GammaArgs ga;
   for (int c = 0; c < 6; ++c) ga.En[c] = (float)(E ? E[c] * (double)g.n : 0.0);
   const double l0 = g.lam0, m0 = g.mu0;
   ga.a = (float)((l0 + m0) / (l0 + 2.0 * m0));
   ga.inv_mu0 = (float)(1.0 / m0);
+  return ga;
+}
+
+static cudaError_t z_pass(const GridDev& g, float2* spec, int mode, const GammaArgs& ga,
+                          cudaStream_t st) {
+  return fused_pencil_ok(g.nz) ? dispatch_fused_pencil(g, spec, mode, ga, st)
+                               : dispatch_pencil(g, spec, mode, ga, st);
+}
+
+// the post-step rides on the fused plane passes; fields are read as float2
+static bool fused_post_ok(const GridDev& g, const float* in, const float* out,
+                          const float2* spec) {
+  return fused_plane_ok(g, spec) && ((uintptr_t)in & 7) == 0 && ((uintptr_t)out & 7) == 0;
+}
+
+int polarization_launches(const GridDev& g, const float* in, const float* out,
+                          const float2* spec) {
+  return fused_post_ok(g, in, out, spec) ? 3 : gamma_launches(g.nx, g.ny) + 1;
+}
+
+cudaError_t launch_polarization_map(const GridDev& g, const float4* post, const float* in,
+                                    float* eb, float* out, float2* spec, const double Eb[6],
+                                    int mode, cudaStream_t st) {
   cudaError_t e;
-  const bool zf = fused_pencil_ok(g.nz);
-  auto zpass = [&]() {
-    return zf ? dispatch_fused_pencil(g, spec, mode, ga, st) : dispatch_pencil(g, spec, mode, ga, st);
-  };
+  if (fused_post_ok(g, in, out, spec)) {
+    const GammaArgs ga = gamma_args(g, Eb);
+    if ((e = dispatch_fused_plane(g, in, out, spec, mode, 0, st)) != cudaSuccess) return e;
+    if ((e = z_pass(g, spec, mode, ga, st)) != cudaSuccess) return e;
+    return dispatch_fused_inv_post(g, out, spec, in, post, st);
+  }
+  if ((e = launch_apply_gamma(g, in, eb, spec, Eb, mode, st)) != cudaSuccess) return e;
+  return launch_polarization_post(g, post, in, eb, out, st);
+}
+
+cudaError_t launch_apply_gamma(const GridDev& g, const float* in, float* out, float2* spec,
+                               const double E[6], int mode, cudaStream_t st) {
+  const GammaArgs ga = gamma_args(g, E);
+  cudaError_t e;
+  auto zpass = [&]() { return z_pass(g, spec, mode, ga, st); };
   if (fused_plane_ok(g, spec)) {
     if ((e = dispatch_fused_plane(g, in, out, spec, mode, 0, st)) != cudaSuccess) return e;
     if ((e = zpass()) != cudaSuccess) return e;

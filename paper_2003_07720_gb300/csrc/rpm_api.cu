@@ -58,7 +58,7 @@ struct rpm_ctx {
   GridDev g{};
   GridDev gb{};                      // g with the Algorithm 3 pre-step table (s_b)
   float2* dmat_b = nullptr;          // per phase (alpha lam - beta lam0, alpha mu - beta mu0)
-  float4* post = nullptr;            // per phase (lam_a, mu_a, lam_s, mu_s) of Algorithm 3
+  float4* post = nullptr;            // per phase (lam_a, mu_a, k_s, h_s) of Algorithm 3
   GridDev gp{};                      // g with the table (-lam0, -mu0): compatible projection
   float2* dmat_p = nullptr;
   long long n = 0;
@@ -193,8 +193,9 @@ cudaError_t upload_scheme_tables(rpm_ctx* c) {
   for (size_t i = 0; i < c->phases.size(); ++i) {
     const double l = c->phases[i].lambda, m = c->phases[i].mu;
     db[i] = make_float2((float)(a * l - b * l0), (float)(a * m - b * m0));
-    pt[i] = make_float4((float)(l + (1.0 - b) * l0), (float)(m + (1.0 - b) * m0), (float)(l + l0),
-                        (float)(m + m0));
+    const double ls = l + l0, ms = m + m0;   // C + C0
+    pt[i] = make_float4((float)(l + (1.0 - b) * l0), (float)(m + (1.0 - b) * m0),
+                        (float)(ls / (3.0 * ls + 2.0 * ms)), (float)(0.5 / ms));
   }
   cudaError_t e = cudaMemcpyAsync(c->dmat_b, db.data(), 256 * sizeof(float2),
                                   cudaMemcpyHostToDevice, c->st);
@@ -281,15 +282,14 @@ struct Ops {
   bool fmap(const float* in, float* out, const double* E, bool linear) {
     if (c->opt.scheme == RPM_SCHEME_BASIC) return gamma(in, out, E, linear ? GM_LINEAR : GM_FULL_MAP);
     const size_t m = mark(0);
-    c->launches += gamma_launches(c->g.nx, c->g.ny) + 1;
+    c->launches += polarization_launches(c->gb, in, out, c->spec);
     float* eb = c->fields + 7 * c->fst;
     double Eb[6] = {0, 0, 0, 0, 0, 0};
     if (!linear)
       for (int k = 0; k < 6; ++k) Eb[k] = c->opt.beta * E[k];
-    bool ok = ck(c, launch_apply_gamma(c->gb, in, eb, c->spec, Eb, linear ? GM_LINEAR : GM_FULL_MAP,
-                                       c->st),
-                 "apply_gamma") &&
-              ck(c, launch_polarization_post(c->g, c->post, in, eb, out, c->st), "post");
+    const bool ok = ck(c, launch_polarization_map(c->gb, c->post, in, eb, out, c->spec, Eb,
+                                                  linear ? GM_LINEAR : GM_FULL_MAP, c->st),
+                       "polarization map");
     done(m);
     return ok;
   }

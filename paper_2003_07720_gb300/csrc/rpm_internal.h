@@ -46,6 +46,18 @@ struct GridDev {
 cudaError_t launch_apply_gamma(const GridDev& g, const float* in, float* out, float2* spec,
                                const double E[6], int mode, cudaStream_t st);
 
+// Algorithm 3 as one map application: eps_b = the Gamma0 map of `in` under g
+// (whose material table holds s_b's moduli, E = Eb), then the post-step
+// out = (C + C0)^-1 : (s_a(in) + C0 : eps_b) with the per-phase table `post`
+// (see launch_polarization_post).  On the fused plane passes the post-step
+// is the last pass's epilogue and eb is not touched; otherwise eb is the
+// scratch of a separate post-step launch.
+cudaError_t launch_polarization_map(const GridDev& g, const float4* post, const float* in,
+                                    float* eb, float* out, float2* spec, const double Eb[6],
+                                    int mode, cudaStream_t st);
+int polarization_launches(const GridDev& g, const float* in, const float* out,
+                          const float2* spec);
+
 bool grid_supported(int nx, int ny, int nz);
 int gamma_launches(int nx, int ny);   // kernels per Gamma0 application (3 or 5)
 int pencil_tile(const GridDev& g);    // pencils per pass-B block for g.pencil_t
@@ -76,7 +88,8 @@ cudaError_t launch_stress(const GridDev& g, const float* eps, float* sig /*nulla
                           double* partials, int nblk, cudaStream_t st);
 cudaError_t launch_fill(float* f, const double E[6], long long n, cudaStream_t st);
 // Algorithm 3's last step: out = (C + C0)^-1 : (s_a(eps) + C0 : eps_b), with per-phase
-// table post[r] = (lam_a, mu_a, lam_s, mu_s); s_a = lam_a tr(eps) I + 2 mu_a eps.
+// table post[r] = (lam_a, mu_a, k_s, h_s); s_a = lam_a tr(eps) I + 2 mu_a eps and
+// (C + C0) = (lam_s, mu_s), k_s = lam_s / (3 lam_s + 2 mu_s), h_s = 1 / (2 mu_s).
 cudaError_t launch_polarization_post(const GridDev& g, const float4* post, const float* eps,
                                      const float* eps_b, float* out, cudaStream_t st);
 cudaError_t launch_newton(const double* sums, int p, const double* M, double* c, double* res_out,

@@ -191,11 +191,32 @@ def test_failure_paths(rpm):
     assert ei.value.status == rpm.RPM_ERR_OOM
 
 
+def _three_phase_cell(shape, seed):
+    """Voxel-wise random three-phase cell with different Poisson ratios, so
+    that every per-phase modulus of Algorithm 3's tables differs."""
+    ph = ms.random_two_phase(shape, seed, 0.3) + ms.random_two_phase(shape, seed + 1, 0.2)
+    lm = [ms.lame(E, nu) for E, nu in ((1.0, 0.3), (10.0, 0.2), (0.3, 0.4))]
+    l0, m0 = ms.lame(2.0, 0.3)
+    return ms.Cell(phase=ph.astype(np.uint8), lam=np.array([a for a, _ in lm]),
+                   mu=np.array([b for _, b in lm]), lam0=l0, mu0=m0)
+
+
+# 32^3 runs the separate post-step; the square planes of 48, 64 and 128
+# run it inside the last pass (clusters of three blocks), nz = 32 included
+POL_CELLS = {
+    "sphere32": lambda: ms.cell_sphere32(32),
+    "three_phase_48": lambda: _three_phase_cell((48, 48, 48), 21),
+    "three_phase_32x64x64": lambda: _three_phase_cell((32, 64, 64), 23),
+    "sphere128": lambda: ms.cell_sphere32(128),
+}
+
+
 @pytest.mark.parametrize("alpha,beta", [(2.0, 2.0), (1.5, 1.0)])
-def test_polarization_map_matches_oracle(rpm, alpha, beta):
+@pytest.mark.parametrize("which", list(POL_CELLS))
+def test_polarization_map_matches_oracle(rpm, alpha, beta, which):
     """One application of Algorithm 3 on the GPU (warm start x, one step)
     against the oracle's map, element by element."""
-    cell = ms.cell_sphere32(32)
+    cell = POL_CELLS[which]()
     prob = o.Problem.from_cell(cell)
     E = ms.unit_strain(0)
     rng = np.random.Generator(np.random.PCG64(4))
