@@ -359,7 +359,7 @@ __device__ __forceinline__ void pass_b_body(const GridDev& g, float2* __restrict
       for (int c = 0; c < 6; ++c) tv[c] = make_float2(0.f, 0.f);
     } else {
       const float x1 = q.x, x2 = q.y, x3 = mz * g.inv_lz;
-      const float inv = 1.f / sqrtf(x1 * x1 + x2 * x2 + x3 * x3);
+      const float inv = rsqrtf(x1 * x1 + x2 * x2 + x3 * x3);
       green_apply(tv, x1 * inv, x2 * inv, x3 * inv, ga.a, ga.inv_mu0);
     }
 #pragma unroll
@@ -473,6 +473,12 @@ __global__ void __launch_bounds__(kPlaneThreads, Split<NX / 2>::N1 >= 16 ? 2 : k
   const float2* in2 = reinterpret_cast<const float2*>(in) + (size_t)z * NY * NXH;
   const uchar2* ph2 = reinterpret_cast<const uchar2*>(g.phase) + (size_t)z * NY * NXH;
   const bool three = mode != GM_RAW_TAU && c < 3;
+  // With at most two phases the material table is two register pairs and a
+  // select (phase ids are < n_phases), which takes the table lookups off the
+  // shared-memory pipe.
+  const bool two = g.n_phases <= 2;
+  const float2 dm0 = dm[0], dm1 = dm[1];
+  auto dmat = [&](unsigned char id) { return two ? (id ? dm1 : dm0) : dm[id]; };
   for (int q = threadIdx.x; q < NY * X2; q += blockDim.x) {
     int y, n2;
     row_task<X2, NY>(q, y, n2);
@@ -491,7 +497,7 @@ __global__ void __launch_bounds__(kPlaneThreads, Split<NX / 2>::N1 >= 16 ? 2 : k
         if (mode == GM_RAW_TAU) {
           v[i] = a[i];
         } else {
-          const float2 d0 = dm[ph[i].x], d1 = dm[ph[i].y];
+          const float2 d0 = dmat(ph[i].x), d1 = dmat(ph[i].y);
           v[i] = make_float2(2.f * d0.y * a[i].x, 2.f * d1.y * a[i].y);
         }
       }
@@ -511,7 +517,7 @@ __global__ void __launch_bounds__(kPlaneThreads, Split<NX / 2>::N1 >= 16 ? 2 : k
         }
 #pragma unroll
         for (int j = 0; j < H; ++j) {
-          const float2 d0 = dm[ph[j].x], d1 = dm[ph[j].y];
+          const float2 d0 = dmat(ph[j].x), d1 = dmat(ph[j].y);
           const float2 e = c == 0 ? a[j] : (c == 1 ? b[j] : d[j]);
           v[i0 + j] = make_float2(fmaf(d0.x, a[j].x + b[j].x + d[j].x, 2.f * d0.y * e.x),
                                   fmaf(d1.x, a[j].y + b[j].y + d[j].y, 2.f * d1.y * e.y));
@@ -990,7 +996,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_pencil_green(GridDev g, float2*
       float n1 = 0.f, n2 = 0.f, n3 = 0.f;
       if (!zero_f) {
         const float x1 = q.x, x2 = q.y, x3 = mz * g.inv_lz;
-        const float inv = 1.f / sqrtf(x1 * x1 + x2 * x2 + x3 * x3);
+        const float inv = rsqrtf(x1 * x1 + x2 * x2 + x3 * x3);
         n1 = x1 * inv;
         n2 = x2 * inv;
         n3 = x3 * inv;
