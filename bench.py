@@ -404,14 +404,33 @@ def run_ours(args):
     dev_ms_max = max_over_ranks(dev_ms, "cuda")
     value = world * args.steps / (dev_ms_max / 1e3)
 
+    # The same solves without the library's event records around every launch
+    # group (opt.profile, which the kernel-class rooflines below come from):
+    # what the records cost inside the timed region.
+    unprofiled = None
+    if world == 1:
+        opts_np = rpm.rpm_default_options(**{f: getattr(opts, f) for f, _ in opts._fields_})
+        opts_np.profile = 0
+        rpm.rpm_set_options(ctx.handle, opts_np)
+        np_ms, _ = time_solves(ctx, E, args.steps, 1, stream, flush, eps_out, raise_ok)
+        rpm.rpm_set_options(ctx.handle, opts)
+        unprofiled = {"value": round(args.steps / (np_ms / 1e3), 4), "unit": UNIT,
+                      "ms_per_step": round(np_ms / args.steps, 3),
+                      "note": "same timed solves with opt.profile = 0 (no per-launch-group "
+                              "event records); the headline keeps them for the rooflines"}
+
     # Kernel classes and their rooflines, from CUDA events the library records
     # on this stream around every launch group during the timed steps.
     launches = sum(i["launches"] for i in infos)
     pk = peaks()
     classes = kernel_classes(infos, N ** 3, pk)
     gamma_line, proj_line = classes["gamma_apply"], classes["projections"]
-    tr = recorded_traffic("gamma_apply_128")
+    # DRAM bytes per application from the ncu record of the map the timed form
+    # applies most: Algorithm 3's map in the warm form, Eq. 3.9 in the cold form
+    tr_key = f"polarization_map_{N}" if args.form == "warm" else f"gamma_apply_{N}"
+    tr = recorded_traffic(tr_key)
     gamma_line["traffic"] = tr
+    gamma_line["traffic_record"] = tr_key
     gamma_line["dram_gbs_from_traffic"] = (round(tr / (gamma_line["avg_launch_ms"] / 1e3) / 1e9, 1)
                                            if tr else None)
     dominant = proj_line if proj_line["total_ms"] >= gamma_line["total_ms"] else gamma_line
@@ -436,6 +455,7 @@ def run_ours(args):
                 "oracle_rel_err": oracle_error("cold", c_inf[0]["mean_stress"]),
                 "launches_per_solve": c_inf[0]["launches"],
                 "roofline_classes": kernel_classes(c_inf, N ** 3, pk)}
+        cold["roofline_classes"]["gamma_apply"]["traffic"] = recorded_traffic(f"gamma_apply_{N}")
 
     # the same form with the RPM stage's reference medium at 2x the matrix
     c0x2 = None
@@ -503,6 +523,7 @@ def run_ours(args):
                     "residual": [i["residual"] for i in infos][:3],
                     "mean_stress_11": infos[0]["mean_stress"][0],
                     "cold_start": cold,
+                    "without_event_records": unprofiled,
                     "c0_2x_matrix": c0x2,
                     "nearvoid_1e-6_c0_sweep": nearvoid,
                     "oracle_rel_err": oracle_error(args.form, infos[0]["mean_stress"]),

@@ -32,6 +32,7 @@ def test_oracle_error_against_the_stored_solve():
 def test_recorded_traffic_is_gated_by_the_kernel_sources():
     # the record matches the current sources (it is re-keyed with every capture)
     assert bench.recorded_traffic("gamma_apply_128") is not None
+    assert bench.recorded_traffic("polarization_map_128") is not None
     assert bench.recorded_traffic("no_such_kernel") is None
 
 
