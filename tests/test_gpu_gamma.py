@@ -57,7 +57,8 @@ def _run(cell, mode, nyq=0, seed=1, E=None):
                                    # fused plane and pencil kernels (square planes 48-128,
                                    # nz 32-128), alone and with the original ones
                                    (128, 64, 64), (64, 96, 96), (32, 128, 128), (48, 64, 64),
-                                   (128, 48, 48), (96, 32, 64), (64, 128, 128), (6, 96, 96)])
+                                   (128, 48, 48), (96, 32, 64), (64, 128, 128), (6, 96, 96),
+                                   (256, 48, 48), (256, 16, 32)])
 @pytest.mark.parametrize("mode", [0, 1, 2])
 def test_apply_gamma_matches_oracle(shape, mode):
     got, ref = _run(_cell(shape, 3), mode)
