@@ -89,9 +89,17 @@ typedef struct {
   int warm_p_max;        /* RPM basis of the warm-start stage (default 0: plain Algorithm 3) */
   int warm_from_eps0;    /* 0 (default): a caller eps0 replaces the warm-start stage;
                             1: the stage runs from eps0 (e.g. a learned guess) */
-  int autotune;          /* 1: rpm_create times the z-pass tile variants (half, default
-                            and twice the pencils per block) on the context's grid and
-                            keeps the fastest; 0 (default): the default tile */
+  int autotune;          /* 1: rpm_create times every available pair of plane-pass and
+                            z-pass variants below on the context's grid and keeps the
+                            fastest (rpm_set_options then keeps that choice while
+                            autotune stays 1); 0 (default): the variants below */
+  int plane_variant;     /* x/y passes: 0 (default) the fused plane kernels where the
+                            grid has them (square planes 48-128), else as 1; 1 the
+                            whole-plane kernels where the plane fits (nx = ny <= 128),
+                            else as 2; 2 the five-pass row and y-pencil kernels */
+  int pencil_variant;    /* z pass: 0 (default) the fused register-resident kernel where
+                            the grid has it (nz 32-128), else the default tile; 1 half,
+                            2 twice the default pencils per block; 3 the default tile */
 } rpm_options;
 
 /* Fixed-point map wrapped by the solver.  BASIC: Eq. 3.9 (Algorithm 1).
@@ -280,6 +288,11 @@ const char* rpm_status_string(rpm_status s);
 /* Pencils per block of the z pass in use (the autotuner's choice when
  * options.autotune was set at creation); 0 for a null context. */
 int rpm_pencil_tile(const rpm_ctx* ctx);
+
+/* Plane-pass kernels in use: 0 fused, 1 whole-plane, 2 five-pass (the
+ * autotuner's choice when options.autotune was set at creation); -1 for a
+ * null context. */
+int rpm_plane_variant(const rpm_ctx* ctx);
 
 /* Device bytes held by the context. */
 size_t rpm_device_bytes(const rpm_ctx* ctx);

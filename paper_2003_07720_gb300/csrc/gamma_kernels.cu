@@ -1606,7 +1606,7 @@ static cudaError_t launch_fused_pencil(const GridDev& g, float2* spec, int mode,
 }
 
 static bool fused_plane_ok(const GridDev& g, const float2* spec) {
-  if (g.nx != g.ny || ((uintptr_t)spec & 15) != 0) return false;
+  if (g.nx != g.ny || ((uintptr_t)spec & 15) != 0) return false;   // pass C's bulk copy
   switch (g.nx) {
 #define RPM_CASE(N) case N:
     RPM_FUSED_PLANE_SIZES(RPM_CASE)
@@ -1731,10 +1731,24 @@ static cudaError_t dispatch_pencil(const GridDev& g, float2* spec, int mode, con
   }
 }
 
-int gamma_launches(int nx, int ny) { return plane_fits(nx, ny) ? 3 : 5; }
+// The plane kernels g.plane_v resolves to on this grid: 0 fused, 1 whole-plane, 2 five-pass.
+static int plane_path(const GridDev& g, const float2* spec) {
+  if (g.plane_v == 0 && fused_plane_ok(g, spec)) return 0;
+  if (g.plane_v <= 1 && plane_fits(g.nx, g.ny)) return 1;
+  return 2;
+}
+
+static bool fused_z(const GridDev& g) { return g.pencil_t == 0 && fused_pencil_ok(g.nz); }
+
+bool fused_z_pass(const GridDev& g) { return fused_z(g); }
+
+// (for a spectrum buffer from cudaMalloc, whose alignment is 256 bytes)
+int plane_variant(const GridDev& g) { return plane_path(g, nullptr); }
+
+int gamma_launches(const GridDev& g) { return plane_variant(g) == 2 ? 5 : 3; }
 
 int pencil_tile(const GridDev& g) {
-  if (fused_pencil_ok(g.nz)) return 128 / split_n1(g.nz);
+  if (fused_z(g)) return 128 / split_n1(g.nz);
   int t0;
   switch (g.nz) {
 #define RPM_CASE(N) \
@@ -1762,19 +1776,19 @@ static GammaArgs gamma_args(const GridDev& g, const double E[6]) {
 
 static cudaError_t z_pass(const GridDev& g, float2* spec, int mode, const GammaArgs& ga,
                           cudaStream_t st) {
-  return fused_pencil_ok(g.nz) ? dispatch_fused_pencil(g, spec, mode, ga, st)
-                               : dispatch_pencil(g, spec, mode, ga, st);
+  return fused_z(g) ? dispatch_fused_pencil(g, spec, mode, ga, st)
+                    : dispatch_pencil(g, spec, mode, ga, st);
 }
 
 // the post-step rides on the fused plane passes; fields are read as float2
 static bool fused_post_ok(const GridDev& g, const float* in, const float* out,
                           const float2* spec) {
-  return fused_plane_ok(g, spec) && ((uintptr_t)in & 7) == 0 && ((uintptr_t)out & 7) == 0;
+  return plane_path(g, spec) == 0 && ((uintptr_t)in & 7) == 0 && ((uintptr_t)out & 7) == 0;
 }
 
 int polarization_launches(const GridDev& g, const float* in, const float* out,
                           const float2* spec) {
-  return fused_post_ok(g, in, out, spec) ? 3 : gamma_launches(g.nx, g.ny) + 1;
+  return fused_post_ok(g, in, out, spec) ? 3 : gamma_launches(g) + 1;
 }
 
 cudaError_t launch_polarization_map(const GridDev& g, const float4* post, const float* in,
@@ -1796,12 +1810,13 @@ cudaError_t launch_apply_gamma(const GridDev& g, const float* in, float* out, fl
   const GammaArgs ga = gamma_args(g, E);
   cudaError_t e;
   auto zpass = [&]() { return z_pass(g, spec, mode, ga, st); };
-  if (fused_plane_ok(g, spec)) {
+  const int path = plane_path(g, spec);
+  if (path == 0) {
     if ((e = dispatch_fused_plane(g, in, out, spec, mode, 0, st)) != cudaSuccess) return e;
     if ((e = zpass()) != cudaSuccess) return e;
     return dispatch_fused_plane(g, in, out, spec, mode, 1, st);
   }
-  if (plane_fits(g.nx, g.ny)) {
+  if (path == 1) {
     if ((e = dispatch_plane(g, in, out, spec, mode, 0, st)) != cudaSuccess) return e;
     if ((e = zpass()) != cudaSuccess) return e;
     return dispatch_plane(g, in, out, spec, mode, 1, st);

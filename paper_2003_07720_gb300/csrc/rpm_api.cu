@@ -120,7 +120,8 @@ bool valid_options(const rpm_options& o) {
          std::isfinite(o.alpha) && std::isfinite(o.beta) && std::isfinite(o.warm_tol) &&
          o.warm_c0_scale > 0 && o.warm_max_iters >= 0 && o.warm_p_max >= 0 &&
          o.warm_p_max <= kPCap && (o.warm_from_eps0 == 0 || o.warm_from_eps0 == 1) &&
-         (o.autotune == 0 || o.autotune == 1);
+         (o.autotune == 0 || o.autotune == 1) && o.plane_variant >= 0 &&
+         o.plane_variant <= 2 && o.pencil_variant >= 0 && o.pencil_variant <= 3;
 }
 
 // Per-phase (lam - lam0, mu - mu0) for the polarization of pass A.
@@ -135,8 +136,14 @@ cudaError_t upload_dmat(rpm_ctx* c) {
 
 cudaError_t upload_scheme_tables(rpm_ctx* c);
 
+void set_variants(rpm_ctx* c, int plane_v, int pencil_t) {
+  c->g.plane_v = c->gb.plane_v = c->gp.plane_v = plane_v;
+  c->g.pencil_t = c->gb.pencil_t = c->gp.pencil_t = pencil_t;
+}
+
 // Tile autotuner: time one Gamma0 application (linear part, zeroed fields)
-// with each z-pass tile variant on this context's grid, keep the fastest.
+// with every distinct pair of plane-pass and z-pass variants on this
+// context's grid, keep the fastest.
 bool autotune_tiles(rpm_ctx* c) {
   float* in = c->fields;
   float* out = c->fields + c->fst;
@@ -145,10 +152,15 @@ bool autotune_tiles(rpm_ctx* c) {
           "autotune"))
     return false;
   float best = 1e30f;
-  int best_v = 0;
-  for (int v = 0; v < 3; ++v) {
+  int best_pl = 0, best_v = 0;
+  std::vector<std::pair<int, int>> seen;   // (plane kernels, pencils per block; -1: fused z)
+  for (int k = 0; k < 12; ++k) {
     GridDev g = c->g;
-    g.pencil_t = v;
+    g.plane_v = k / 4;
+    g.pencil_t = k % 4;
+    const std::pair<int, int> key(plane_variant(g), fused_z_pass(g) ? -1 : pencil_tile(g));
+    if (std::find(seen.begin(), seen.end(), key) != seen.end()) continue;
+    seen.push_back(key);
     if (launch_apply_gamma(g, in, out, c->spec, nullptr, GM_LINEAR, c->st) != cudaSuccess) {
       cudaGetLastError();   // variant not available on this grid (shared memory)
       continue;
@@ -165,10 +177,11 @@ bool autotune_tiles(rpm_ctx* c) {
       return false;
     if (ms < best) {
       best = ms;
-      best_v = v;
+      best_pl = g.plane_v;
+      best_v = g.pencil_t;
     }
   }
-  c->g.pencil_t = c->gb.pencil_t = c->gp.pencil_t = best_v;
+  set_variants(c, best_pl, best_v);
   return true;
 }
 
@@ -273,7 +286,7 @@ struct Ops {
   }
   bool gamma(const float* in, float* out, const double* E, int mode) {
     const size_t m = mark(0);
-    c->launches += gamma_launches(c->g.nx, c->g.ny);
+    c->launches += gamma_launches(c->g);
     const bool ok = ck(c, launch_apply_gamma(c->g, in, out, c->spec, E, mode, c->st), "apply_gamma");
     done(m);
     return ok;
@@ -363,6 +376,8 @@ void rpm_default_options(rpm_options* o) {
   o->warm_p_max = 0;
   o->warm_from_eps0 = 0;
   o->autotune = 0;
+  o->plane_variant = 0;
+  o->pencil_variant = 0;
 }
 
 int rpm_grid_supported(int nx, int ny, int nz) { return grid_supported(nx, ny, nz) ? 1 : 0; }
@@ -436,9 +451,11 @@ rpm_status rpm_set_options(rpm_ctx* c, const rpm_options* o) {
   if (!c || !o) return fail(c, RPM_ERR_INVALID_ARG, "null argument");
   if (!valid_options(*o) || o->p_max > c->p_cap)
     return fail(c, RPM_ERR_INVALID_ARG, "invalid options (p_max above the creation value?)");
+  const bool keep_tuned = c->opt.autotune && o->autotune;
   c->opt = *o;
   c->g.nyquist = o->nyquist;
   c->gb.nyquist = c->gp.nyquist = o->nyquist;
+  if (!keep_tuned) set_variants(c, o->plane_variant, o->pencil_variant);
   if (!ck(c, upload_scheme_tables(c), "scheme tables")) return RPM_ERR_CUDA;
   return RPM_OK;
 }
@@ -596,6 +613,7 @@ rpm_status rpm_create(const rpm_grid* grid, const uint8_t* phase, int phase_on_d
   c->gb.dmat = c->dmat_b;
   c->gp = g;
   c->gp.dmat = c->dmat_p;
+  set_variants(c, o.plane_variant, o.pencil_variant);
   if (!ck(c, upload_scheme_tables(c), "scheme tables")) {
     rpm_destroy(c);
     return RPM_ERR_CUDA;
@@ -612,6 +630,8 @@ rpm_status rpm_create(const rpm_grid* grid, const uint8_t* phase, int phase_on_d
 }
 
 int rpm_pencil_tile(const rpm_ctx* c) { return c ? pencil_tile(c->g) : 0; }
+
+int rpm_plane_variant(const rpm_ctx* c) { return c ? plane_variant(c->g) : -1; }
 
 rpm_status rpm_set_trace(rpm_ctx* c, double* residuals, int* basis_sizes, int capacity) {
   if (!c || capacity < 0) return fail(c, RPM_ERR_INVALID_ARG, "bad trace arguments");
@@ -630,7 +650,7 @@ rpm_status rpm_apply_gamma(rpm_ctx* c, const float* in, const double E[6], float
   if (in == out) return fail(c, RPM_ERR_INVALID_ARG, "in and out alias");
   if (flags == RPM_GAMMA_PROJECT) {
     // E - Gamma0 * ((-C0) : in) = E + Gamma0 * (C0 : in): the pass-A table of gp
-    c->launches += gamma_launches(c->g.nx, c->g.ny);
+    c->launches += gamma_launches(c->g);
     if (!ck(c, launch_apply_gamma(c->gp, in, out, c->spec, E, GM_FULL_MAP, c->st), "project"))
       return RPM_ERR_CUDA;
     return RPM_OK;

@@ -36,7 +36,9 @@ struct GridDev {
   float lam0, mu0;
   float inv_lx, inv_ly, inv_lz;   // 1 / L_j (frequency scaling)
   int nyquist;           // 0: zero mixed Nyquist frequencies, 1: signed
-  int pencil_t;          // pass-B tile variant: 0 default, 1 half, 2 twice the pencils
+  int plane_v;           // x/y passes: 0 fused where available, 1 whole-plane, 2 five-pass
+  int pencil_t;          // z pass: 0 fused where available, else the default tile;
+                         // 1 half, 2 twice the default pencils; 3 the default tile
   int* err;              // device flag set to 1 when a bounded wait of a kernel gave up
 };
 
@@ -59,8 +61,10 @@ int polarization_launches(const GridDev& g, const float* in, const float* out,
                           const float2* spec);
 
 bool grid_supported(int nx, int ny, int nz);
-int gamma_launches(int nx, int ny);   // kernels per Gamma0 application (3 or 5)
-int pencil_tile(const GridDev& g);    // pencils per pass-B block for g.pencil_t
+int gamma_launches(const GridDev& g);  // kernels per Gamma0 application (3 or 5)
+int pencil_tile(const GridDev& g);     // pencils per pass-B block for g.pencil_t
+int plane_variant(const GridDev& g);   // plane kernels g.plane_v resolves to (0, 1, 2)
+bool fused_z_pass(const GridDev& g);   // g.pencil_t resolves to the fused z kernel
 
 // ---- field kernels (field_kernels.cu) -------------------------------------
 // Partial sums per block, then one finishing block; see the definitions.

@@ -53,7 +53,8 @@ class rpm_options(ctypes.Structure):
                 ("scheme", ctypes.c_int), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
                 ("warm_tol", ctypes.c_double), ("warm_c0_scale", ctypes.c_double),
                 ("warm_max_iters", ctypes.c_int), ("warm_p_max", ctypes.c_int),
-                ("warm_from_eps0", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("warm_from_eps0", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("plane_variant", ctypes.c_int), ("pencil_variant", ctypes.c_int)]
 
 
 class rpm_solve_info(ctypes.Structure):
@@ -87,7 +88,7 @@ EXPORTS = ("rpm_default_options", "rpm_create", "rpm_set_phase", "rpm_set_option
            "rpm_apply_gamma", "rpm_solve", "rpm_effective_stiffness", "rpm_last_error",
            "rpm_status_string", "rpm_device_bytes", "rpm_grid_supported", "rpm_destroy",
            "rpm_set_trace", "rpm_set_materials", "rpm_effective_stiffness_batch",
-           "rpm_pencil_tile")
+           "rpm_pencil_tile", "rpm_plane_variant")
 
 
 def lib():
@@ -134,6 +135,8 @@ def lib():
     L.rpm_effective_stiffness_batch.restype = ctypes.c_int
     L.rpm_pencil_tile.argtypes = [vp]
     L.rpm_pencil_tile.restype = ctypes.c_int
+    L.rpm_plane_variant.argtypes = [vp]
+    L.rpm_plane_variant.restype = ctypes.c_int
     L.rpm_destroy.argtypes = [vp]
     L.rpm_destroy.restype = None
     _lib = L
@@ -291,6 +294,11 @@ def rpm_effective_stiffness_batch(cells, options: rpm_options | None = None, n_w
 def rpm_pencil_tile(ctx) -> int:
     """Pencils per block of the z pass in use (the autotuner's choice)."""
     return int(lib().rpm_pencil_tile(ctx))
+
+
+def rpm_plane_variant(ctx) -> int:
+    """Plane-pass kernels in use: 0 fused, 1 whole-plane, 2 five-pass."""
+    return int(lib().rpm_plane_variant(ctx))
 
 
 def rpm_device_bytes(ctx) -> int:
