@@ -219,11 +219,13 @@ struct GammaArgs {
 };
 
 // T consecutive (ky, kx) pencils per pass-B block: TT = 0 takes the default
-// for the length (8 pencils = 64-byte rows at nz >= 128); the tile autotuner
-// of rpm_create also tries half and twice the default (GridDev::pencil_t).
+// for the length (8 pencils = 64-byte rows at nz = 128; 16 at nz = 256, one
+// 512-thread block per SM, measured 0.980 vs 1.012 ms per 256^3 apply with
+// 8); the tile autotuner of rpm_create also tries half and twice the
+// default (GridDev::pencil_t).
 template <int NZ, int TT = 0>
 struct PencilCfg {
-  static constexpr int T = TT ? TT : (NZ >= 128 ? 8 : (NZ >= 64 ? 16 : 32));
+  static constexpr int T = TT ? TT : (NZ >= 256 ? 16 : (NZ >= 128 ? 8 : (NZ >= 64 ? 16 : 32)));
   static constexpr int NZP = (NZ % 2 == 0) ? NZ + 1 : NZ;
 };
 
