@@ -52,6 +52,7 @@ E_INCL = 1e-3                       # inclusion modulus (matrix E = 1); see the 
 WARM_TOL = 1e-4                     # increment at which the warm-start stage hands over
 BYTES_PER_VOXEL_GAMMA = 49          # read eps 24 B + phase 1 B, write xi 24 B
 L2_FLUSH_BYTES = 256 << 20
+PROFILE_EVERY = 16                  # launch groups per CUDA-event sample (opt.profile)
 
 
 def workload_config(extra: dict | None = None) -> dict:
@@ -302,7 +303,8 @@ def time_solves(ctx, E, steps, warmup, stream, flush, eps_out, raise_ok=True):
 
 def kernel_classes(infos, n_vox: int, pk: dict) -> dict:
     """Rooflines of the two kernel classes of a set of solves, from the CUDA
-    events the library records around every launch group (opt.profile): the
+    events the library records around every k-th launch group of each class
+    (opt.profile = k; the sampled time scaled to all groups): the
     Gamma0 application (algorithmic 49 B/voxel per application) and the
     projections (the bytes the library counts for each dots/combine launch)."""
     gamma_ms = sum(i["gamma_ms"] for i in infos)
@@ -371,7 +373,9 @@ def run_ours(args):
 
     cell = ms.cell_nearvoid(N, rank_seed(rank), c0_scale=1.0, e_incl=E_INCL)
     E = ms.unit_strain(0)
-    opts = rpm.rpm_default_options(tol=TOL, p_max=P_MAX, n_max=10, profile=1)
+    # kernel-class times from CUDA events around every PROFILE_EVERY-th launch
+    # group of each class (bracketing every group costs 5 % of the solve)
+    opts = rpm.rpm_default_options(tol=TOL, p_max=P_MAX, n_max=10, profile=PROFILE_EVERY)
     if args.max_iters:
         opts.max_iters = args.max_iters          # profiling captures only (not converged)
     if args.scheme == "polarization":
@@ -404,9 +408,9 @@ def run_ours(args):
     dev_ms_max = max_over_ranks(dev_ms, "cuda")
     value = world * args.steps / (dev_ms_max / 1e3)
 
-    # The same solves without the library's event records around every launch
-    # group (opt.profile, which the kernel-class rooflines below come from):
-    # what the records cost inside the timed region.
+    # The same solves without the library's event records (opt.profile, which
+    # the kernel-class rooflines below come from): what the sampled records
+    # cost inside the timed region.
     unprofiled = None
     if world == 1:
         opts_np = rpm.rpm_default_options(**{f: getattr(opts, f) for f, _ in opts._fields_})
@@ -416,11 +420,12 @@ def run_ours(args):
         rpm.rpm_set_options(ctx.handle, opts)
         unprofiled = {"value": round(args.steps / (np_ms / 1e3), 4), "unit": UNIT,
                       "ms_per_step": round(np_ms / args.steps, 3),
-                      "note": "same timed solves with opt.profile = 0 (no per-launch-group "
-                              "event records); the headline keeps them for the rooflines"}
+                      "note": "same timed solves with opt.profile = 0 (no event records); "
+                              "the headline brackets every %d-th launch group of each class "
+                              "with CUDA events for the rooflines" % PROFILE_EVERY}
 
     # Kernel classes and their rooflines, from CUDA events the library records
-    # on this stream around every launch group during the timed steps.
+    # on this stream around a sample of launch groups during the timed steps.
     launches = sum(i["launches"] for i in infos)
     pk = peaks()
     classes = kernel_classes(infos, N ** 3, pk)

@@ -73,7 +73,8 @@ typedef struct {
   int nyquist;           /* RPM_NYQ_ZERO_MIXED (the only accepted value) */
   double diverge_factor; /* RPM_ERR_DIVERGED when residual > factor * initial, 1e10 */
   double max_device_gb;  /* refuse contexts needing more device memory; 0 = no cap */
-  int profile;           /* 1: time Gamma0 applications and projections with CUDA events */
+  int profile;           /* k >= 1: time every k-th Gamma0 application and every k-th
+                            projection group with CUDA events (1: all of them); 0: off */
   int scheme;            /* RPM_SCHEME_BASIC (Eq. 3.9, default) or RPM_SCHEME_POLARIZATION */
   double alpha, beta;    /* Algorithm 3 parameters (alpha = beta = 2: Accelerated scheme) */
   /* Warm start (cold start when warm_tol <= 0, the default): before the
@@ -118,8 +119,9 @@ typedef struct {
   double residual0;    /* residual of the initial guess */
   double mean_stress[6]; /* <sigma> of the returned strain field (FP64 sum) */
   float ms;            /* device time of the solve (CUDA events), milliseconds */
-  float gamma_ms;      /* with opt.profile: summed device time of the Gamma0 applications */
-  float proj_ms;       /* with opt.profile: summed time of the projection/combine kernels */
+  float gamma_ms;      /* with opt.profile: device time of the Gamma0 applications (the
+                          timed sample scaled to all of them) */
+  float proj_ms;       /* with opt.profile: the same for the projection/combine kernels */
   long long launches;  /* CUDA kernels launched by the solve */
   double proj_bytes;   /* algorithmic bytes moved by the projection/combine kernels */
   int warm_iters;      /* steps of the warm-start stage (0: cold start) */

@@ -81,10 +81,12 @@ struct rpm_ctx {
   int p = 0;
   long long launches = 0;            // kernels launched by the current solve
   double proj_bytes = 0;             // algorithmic bytes of the projection kernels
-  // event pairs for opt.profile: (start, stop, category 0 = Gamma0, 1 = projections)
+  // event pairs for opt.profile: (start, stop, category 0 = Gamma0, 1 = projections);
+  // groups seen and bracketed per category in the current solve
   std::vector<cudaEvent_t> prof_ev;
   std::vector<int> prof_cat;
   size_t prof_used = 0;
+  long long prof_seen[2] = {0, 0}, prof_rec[2] = {0, 0};
   // optional residual history (host arrays owned by the caller)
   double* trace_res = nullptr;
   int* trace_p = nullptr;
@@ -115,6 +117,7 @@ void build_twiddles(int L, std::vector<float2>& out) {
 
 bool valid_options(const rpm_options& o) {
   return o.n_max >= 1 && o.p_max >= 0 && o.p_max <= kPCap && o.max_iters >= 0 && o.tol >= 0 &&
+         o.profile >= 0 &&
          o.t_ratio >= 0 && o.nyquist == RPM_NYQ_ZERO_MIXED && o.diverge_factor > 0 &&
          (o.scheme == RPM_SCHEME_BASIC || o.scheme == RPM_SCHEME_POLARIZATION) &&
          std::isfinite(o.alpha) && std::isfinite(o.beta) && std::isfinite(o.warm_tol) &&
@@ -269,6 +272,7 @@ struct Ops {
   // optional event bracket around a group of launches (opt.profile)
   size_t mark(int cat) {
     if (!c->opt.profile) return (size_t)-1;
+    if (c->prof_seen[cat]++ % c->opt.profile != 0) return (size_t)-1;   // every k-th group
     if (c->prof_used * 2 + 2 > c->prof_ev.size()) {
       cudaEvent_t a, b;
       if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return (size_t)-1;
@@ -278,6 +282,7 @@ struct Ops {
     }
     const size_t i = c->prof_used++;
     c->prof_cat[i] = cat;
+    ++c->prof_rec[cat];
     cudaEventRecord(c->prof_ev[2 * i], c->st);
     return i;
   }
@@ -685,6 +690,7 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
   c->launches = 0;
   c->proj_bytes = 0;
   c->prof_used = 0;
+  c->prof_seen[0] = c->prof_seen[1] = c->prof_rec[0] = c->prof_rec[1] = 0;
   c->H.clear();
   std::vector<double> M;
 
@@ -989,6 +995,9 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
     if (cudaEventElapsedTime(&t, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]) != cudaSuccess) continue;
     (c->prof_cat[i] == 0 ? inf.gamma_ms : inf.proj_ms) += t;
   }
+  // sampled groups (opt.profile = k > 1) stand for all groups of their class
+  if (c->prof_rec[0] > 0) inf.gamma_ms *= (float)((double)c->prof_seen[0] / (double)c->prof_rec[0]);
+  if (c->prof_rec[1] > 0) inf.proj_ms *= (float)((double)c->prof_seen[1] / (double)c->prof_rec[1]);
   inf.launches = c->launches;
   inf.proj_bytes = c->proj_bytes;
   inf.iters = it;

@@ -488,3 +488,21 @@ def test_batched_sweep_32_members_ceff_match_oracle(rpm):
         err = np.max(np.abs(C[i] - ref)) / np.max(np.abs(ref))
         bound = max(CEFF_TOL, 4e-8 * g[str(s)]["contrast"])
         assert err < bound, (s, g[str(s)]["contrast"], err)
+
+
+def test_sampled_event_profile_scales_to_all_groups(rpm):
+    """opt.profile = k brackets every k-th launch group of each class with
+    CUDA events and scales the sampled time to all groups: the estimate of
+    the Gamma0 time agrees with the all-groups figure and stays inside the
+    solve's own time."""
+    cell = ms.cell_sphere32(64)
+    E = ms.unit_strain(0)
+    out = {}
+    for k in (1, 4):
+        with rpm.Context(cell, rpm.rpm_default_options(profile=k, p_max=4)) as ctx:
+            ctx.solve(E)   # warm-up
+            _, info = ctx.solve(E)
+        out[k] = info
+        assert 0 < info["gamma_ms"] <= info["ms"]
+    assert out[1]["gamma_applies"] == out[4]["gamma_applies"]
+    assert 0.5 < out[4]["gamma_ms"] / out[1]["gamma_ms"] < 2.0
