@@ -296,6 +296,14 @@ int rpm_pencil_tile(const rpm_ctx* ctx);
  * null context. */
 int rpm_plane_variant(const rpm_ctx* ctx);
 
+/* Self-check of the bounded waits (kernels that wait for an asynchronous
+ * copy give up after about one second and report RPM_ERR_TIMEOUT instead of
+ * hanging): runs one block on `cuda_stream` (NULL: the default stream) whose
+ * barrier wait can never complete.  *gave_up = 1 when the wait gave up by
+ * itself; *waited_ms = the kernel's duration (CUDA events).  Synchronizes
+ * the stream.  Returns RPM_OK, or RPM_ERR_INVALID_ARG / RPM_ERR_CUDA. */
+rpm_status rpm_bounded_wait_check(void* cuda_stream, int* gave_up, float* waited_ms);
+
 /* Device bytes held by the context. */
 size_t rpm_device_bytes(const rpm_ctx* ctx);
 

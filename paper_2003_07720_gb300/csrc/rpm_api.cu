@@ -638,6 +638,29 @@ int rpm_pencil_tile(const rpm_ctx* c) { return c ? pencil_tile(c->g) : 0; }
 
 int rpm_plane_variant(const rpm_ctx* c) { return c ? plane_variant(c->g) : -1; }
 
+rpm_status rpm_bounded_wait_check(void* cuda_stream, int* gave_up, float* waited_ms) {
+  if (!gave_up || !waited_ms) return RPM_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int* d = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  int h = 0;
+  float ms = 0.f;
+  bool ok = cudaMalloc(&d, sizeof(int)) == cudaSuccess &&
+            cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess &&
+            cudaMemsetAsync(d, 0, sizeof(int), st) == cudaSuccess &&
+            cudaEventRecord(a, st) == cudaSuccess && launch_wait_selfcheck(d, st) == cudaSuccess &&
+            cudaEventRecord(b, st) == cudaSuccess &&
+            cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+            cudaStreamSynchronize(st) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess;
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (d) cudaFree(d);
+  if (!ok) return RPM_ERR_CUDA;
+  *gave_up = h;
+  *waited_ms = ms;
+  return RPM_OK;
+}
+
 rpm_status rpm_set_trace(rpm_ctx* c, double* residuals, int* basis_sizes, int capacity) {
   if (!c || capacity < 0) return fail(c, RPM_ERR_INVALID_ARG, "bad trace arguments");
   c->trace_res = residuals;

@@ -60,6 +60,10 @@ cudaError_t launch_polarization_map(const GridDev& g, const float4* post, const 
 int polarization_launches(const GridDev& g, const float* in, const float* out,
                           const float2* spec);
 
+// One block whose asynchronous-copy barrier wait can never complete:
+// out[0] = 1 once the bounded wait has given up by itself.
+cudaError_t launch_wait_selfcheck(int* out, cudaStream_t st);
+
 bool grid_supported(int nx, int ny, int nz);
 int gamma_launches(const GridDev& g);  // kernels per Gamma0 application (3 or 5)
 int pencil_tile(const GridDev& g);     // pencils per pass-B block for g.pencil_t

@@ -88,7 +88,7 @@ EXPORTS = ("rpm_default_options", "rpm_create", "rpm_set_phase", "rpm_set_option
            "rpm_apply_gamma", "rpm_solve", "rpm_effective_stiffness", "rpm_last_error",
            "rpm_status_string", "rpm_device_bytes", "rpm_grid_supported", "rpm_destroy",
            "rpm_set_trace", "rpm_set_materials", "rpm_effective_stiffness_batch",
-           "rpm_pencil_tile", "rpm_plane_variant")
+           "rpm_pencil_tile", "rpm_plane_variant", "rpm_bounded_wait_check")
 
 
 def lib():
@@ -137,6 +137,8 @@ def lib():
     L.rpm_pencil_tile.restype = ctypes.c_int
     L.rpm_plane_variant.argtypes = [vp]
     L.rpm_plane_variant.restype = ctypes.c_int
+    L.rpm_bounded_wait_check.argtypes = [vp, P(ctypes.c_int), P(ctypes.c_float)]
+    L.rpm_bounded_wait_check.restype = ctypes.c_int
     L.rpm_destroy.argtypes = [vp]
     L.rpm_destroy.restype = None
     _lib = L
@@ -299,6 +301,15 @@ def rpm_pencil_tile(ctx) -> int:
 def rpm_plane_variant(ctx) -> int:
     """Plane-pass kernels in use: 0 fused, 1 whole-plane, 2 five-pass."""
     return int(lib().rpm_plane_variant(ctx))
+
+
+def rpm_bounded_wait_check(stream=None) -> tuple[bool, float]:
+    """Run the bounded-wait self-check on `stream`: (gave up by itself, ms waited)."""
+    g, ms = ctypes.c_int(0), ctypes.c_float(0.0)
+    st = lib().rpm_bounded_wait_check(_stream_ptr(stream), ctypes.byref(g), ctypes.byref(ms))
+    if st != RPM_OK:
+        raise RpmError(st, "bounded-wait self-check failed")
+    return bool(g.value), float(ms.value)
 
 
 def rpm_device_bytes(ctx) -> int:

@@ -207,6 +207,7 @@ POL_CELLS = {
     "sphere32": lambda: ms.cell_sphere32(32),
     "three_phase_48": lambda: _three_phase_cell((48, 48, 48), 21),
     "three_phase_32x64x64": lambda: _three_phase_cell((32, 64, 64), 23),
+    "three_phase_48x96x96": lambda: _three_phase_cell((48, 96, 96), 25),
     "sphere128": lambda: ms.cell_sphere32(128),
 }
 
@@ -506,3 +507,18 @@ def test_sampled_event_profile_scales_to_all_groups(rpm):
         assert 0 < info["gamma_ms"] <= info["ms"]
     assert out[1]["gamma_applies"] == out[4]["gamma_applies"]
     assert 0.5 < out[4]["gamma_ms"] / out[1]["gamma_ms"] < 2.0
+
+
+def test_bounded_wait_gives_up_and_the_stream_stays_usable(rpm):
+    """The bulk-copy passes wait on an mbarrier with a bound (about one
+    second on the global timer) and report RPM_ERR_TIMEOUT instead of
+    hanging.  A barrier that no copy completes (a flag that nothing sets)
+    must make the wait give up by itself, and the next launches on the same
+    stream must run normally."""
+    gave_up, ms_waited = rpm.rpm_bounded_wait_check(torch.cuda.current_stream())
+    assert gave_up
+    assert 500.0 < ms_waited < 10000.0, ms_waited
+    cell = ms.cell_sphere32(48)
+    with rpm.Context(cell) as ctx:
+        st, info = ctx.solve(ms.unit_strain(0))
+    assert st == rpm.RPM_OK and info["converged"]
