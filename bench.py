@@ -743,9 +743,11 @@ def run_study_c4(args):
                          "status": rpm.status_name(stat[i]),
                          "converged_loads": int(sum(1 for j in inf if j["converged"])),
                          "steps": [int(j["iters"]) for j in inf],
+                         "basis_reused": [int(j["basis_reused"]) for j in inf],
                          "C_eff": [[float("%.7g" % v) for v in row] for row in C[i]]})
         conv = [r for r in rows if r["converged_loads"] == 6]
         out[name] = {"seconds": round(dt, 3), "solves_per_s": round(6 * len(cells) / dt, 2),
+                     "steps": int(sum(sum(r["steps"]) for r in rows)),
                      "cells_all_loads_converged": len(conv),
                      "solves_converged": int(sum(r["converged_loads"] for r in rows)),
                      "rows": rows}

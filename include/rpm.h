@@ -101,6 +101,15 @@ typedef struct {
   int pencil_variant;    /* z pass: 0 (default) the fused register-resident kernel where
                             the grid has it (nz 32-128), else the default tile; 1 half,
                             2 twice the default pencils per block; 3 the default tile */
+  int share_basis;       /* 1: a solve starts from the unstable basis (Z, W = F_u Z, H)
+                            that an earlier solve of the same map left in the context --
+                            F_u does not depend on the load E, so the six loads of
+                            rpm_effective_stiffness share one basis (block RPM, same fixed
+                            point); the basis is dropped when the phases, materials, C0,
+                            scheme or Nyquist rule change.  Measured slower at p_max 20:
+                            each unit load excites its own part of the slow eigenspace,
+                            and a basis filled by the earlier loads cannot grow to take
+                            it.  0 (default): every solve starts with an empty basis */
 } rpm_options;
 
 /* Fixed-point map wrapped by the solver.  BASIC: Eq. 3.9 (Algorithm 1).
@@ -126,6 +135,7 @@ typedef struct {
   double proj_bytes;   /* algorithmic bytes moved by the projection/combine kernels */
   int warm_iters;      /* steps of the warm-start stage (0: cold start) */
   double warm_residual;/* increment of the warm-start stage when it stopped */
+  int basis_reused;    /* basis vectors taken over from an earlier solve (share_basis) */
 } rpm_solve_info;
 
 /* Fill `opt` with the defaults listed above. */

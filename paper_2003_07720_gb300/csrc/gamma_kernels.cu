@@ -1807,25 +1807,6 @@ cudaError_t launch_polarization_map(const GridDev& g, const float4* post, const 
   return launch_polarization_post(g, post, in, eb, out, st);
 }
 
-// Self-check of the bounded barrier wait the bulk-copy passes rely on: one
-// thread arms an mbarrier for 16 bytes that no copy will ever deliver and
-// waits; the wait must give up by itself (about one second, global timer)
-// and the kernel must return.  out[0] = 1 when it gave up, 0 otherwise.
-__global__ void k_wait_selfcheck(int* out) {
-  __shared__ __align__(8) uint64_t bar;
-  if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
-    mbar_init_fence();
-    mbar_arrive_expect_tx(&bar, 16);
-    out[0] = mbar_wait(&bar, 0) ? 0 : 1;
-  }
-}
-
-cudaError_t launch_wait_selfcheck(int* out, cudaStream_t st) {
-  k_wait_selfcheck<<<1, 32, 0, st>>>(out);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_apply_gamma(const GridDev& g, const float* in, float* out, float2* spec,
                                const double E[6], int mode, cudaStream_t st) {
   const GammaArgs ga = gamma_args(g, E);

@@ -79,6 +79,14 @@ struct rpm_ctx {
   std::string err;
   std::vector<double> H;             // host copy of H = Z^T F_u Z (row-major, p x p)
   int p = 0;
+  // The basis held in Z and W after the last solve that had one: its size,
+  // H, and the map it belongs to (F_u depends on the phases, the materials,
+  // C0 and the scheme, not on the load E); options.share_basis starts the
+  // next solve of the same map from it.
+  int sb_p = 0;
+  std::vector<double> sb_H;
+  std::vector<double> sb_key;
+  long long mat_version = 0;         // bumped by every phase or material change
   long long launches = 0;            // kernels launched by the current solve
   double proj_bytes = 0;             // algorithmic bytes of the projection kernels
   // event pairs for opt.profile: (start, stop, category 0 = Gamma0, 1 = projections);
@@ -124,7 +132,8 @@ bool valid_options(const rpm_options& o) {
          o.warm_c0_scale > 0 && o.warm_max_iters >= 0 && o.warm_p_max >= 0 &&
          o.warm_p_max <= kPCap && (o.warm_from_eps0 == 0 || o.warm_from_eps0 == 1) &&
          (o.autotune == 0 || o.autotune == 1) && o.plane_variant >= 0 &&
-         o.plane_variant <= 2 && o.pencil_variant >= 0 && o.pencil_variant <= 3;
+         o.plane_variant <= 2 && o.pencil_variant >= 0 && o.pencil_variant <= 3 &&
+         (o.share_basis == 0 || o.share_basis == 1);
 }
 
 // Per-phase (lam - lam0, mu - mu0) for the polarization of pass A.
@@ -383,6 +392,7 @@ void rpm_default_options(rpm_options* o) {
   o->autotune = 0;
   o->plane_variant = 0;
   o->pencil_variant = 0;
+  o->share_basis = 0;
 }
 
 int rpm_grid_supported(int nx, int ny, int nz) { return grid_supported(nx, ny, nz) ? 1 : 0; }
@@ -449,6 +459,7 @@ rpm_status rpm_set_phase(rpm_ctx* c, const uint8_t* phase, int on_device) {
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st),
           "phase upload"))
     return RPM_ERR_CUDA;
+  ++c->mat_version;   // a stored basis belongs to the previous cell
   return RPM_OK;
 }
 
@@ -692,6 +703,13 @@ rpm_status rpm_apply_gamma(rpm_ctx* c, const float* in, const double E[6], float
 
 namespace {
 
+// Everything F_u depends on besides the grid: phases and materials (by
+// version), C0, the scheme and its parameters, the Nyquist rule.
+std::vector<double> basis_key(const rpm_ctx* c) {
+  return {(double)c->mat_version, c->c0.lambda, c->c0.mu, (double)c->opt.scheme, c->opt.alpha,
+          c->opt.beta, (double)c->opt.nyquist};
+}
+
 // One solve of Algorithm 2 (Algorithm 1 when p_max = 0).
 rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* eps_out,
                       float* sig_out, int out_on_host, rpm_solve_info* info) {
@@ -719,6 +737,30 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
 
   if (!ck(c, cudaEventRecord(c->ev0, c->st), "event")) return RPM_ERR_CUDA;
   if (!ck(c, cudaMemsetAsync(ds, 0, (kSmall + 1) * 8, c->st), "memset")) return RPM_ERR_CUDA;
+  // A basis of the same map left in Z and W by an earlier solve (another load
+  // E, or the same one): with share_basis the solve starts from its leading
+  // min(size, p_max) vectors, H's leading block and M = (I - H)^-1.
+  const std::vector<double> key = basis_key(c);
+  if (o.share_basis && c->sb_p > 0 && c->sb_key == key) {
+    const int p = std::min(c->sb_p, std::min(o.p_max, c->p_cap));
+    c->H.assign((size_t)p * p, 0.0);
+    std::vector<double> A((size_t)p * p);
+    for (int i = 0; i < p; ++i)
+      for (int j = 0; j < p; ++j) {
+        c->H[(size_t)i * p + j] = c->sb_H[(size_t)i * c->sb_p + j];
+        A[(size_t)i * p + j] = (i == j ? 1.0 : 0.0) - c->H[(size_t)i * p + j];
+      }
+    if (p > 0 && invert(p, A, M)) {
+      if (!ck(c, cudaMemcpyAsync(ds + kM, M.data(), sizeof(double) * p * p,
+                                 cudaMemcpyHostToDevice, c->st),
+              "upload M"))
+        return RPM_ERR_CUDA;
+      c->p = p;
+      inf.basis_reused = p;
+    } else {
+      c->H.clear();
+    }
+  }
   float* eps_cur = epsb[0];
   if (eps0) {
     if (!ck(c, cudaMemcpyAsync(eps_cur, eps0, c->fsz * 4, cudaMemcpyDeviceToDevice, c->st), "eps0"))
@@ -971,6 +1013,12 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
     }
   }
 
+  if (c->p > 0 && (status == RPM_OK || status == RPM_ERR_NOT_CONVERGED)) {
+    c->sb_p = c->p;   // what Z and W now hold, for a later solve of the same map
+    c->sb_H = c->H;
+    c->sb_key = key;
+  }
+
   if (based) {   // eps = base + y
     ++c->launches;
     if (!ck(c, launch_axpby(base, 1.f, base, 1.f, eps_cur, c->n, c->st), "base")) return RPM_ERR_CUDA;
@@ -1135,6 +1183,7 @@ rpm_status rpm_set_materials(rpm_ctx* c, int n_phases, const rpm_iso* phases, rp
     return fail(c, RPM_ERR_INVALID_ARG, "bad reference medium");
   c->phases.assign(phases, phases + n_phases);
   c->g.n_phases = c->gb.n_phases = c->gp.n_phases = n_phases;
+  ++c->mat_version;
   std::vector<float2> cm(256, make_float2(0.f, 0.f));
   for (int i = 0; i < n_phases; ++i)
     cm[i] = make_float2((float)phases[i].lambda, (float)phases[i].mu);
@@ -1161,10 +1210,13 @@ rpm_status rpm_effective_stiffness_batch(const rpm_cell* cells, int n_cells, con
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return RPM_ERR_CUDA;
   // jobs: (cell, load); a worker keeps the cell's phase map and materials
-  // loaded while it takes consecutive loads of the same cell
+  // loaded while it takes consecutive loads of the same cell.  With
+  // share_basis a job is a whole cell, its six loads solved in turn on one
+  // context so that each starts from the basis the previous one left.
   std::atomic<int> next{0};
   std::atomic<int> hard_error{RPM_OK};
-  const int n_jobs = 6 * n_cells;
+  const int per_job = o.share_basis ? 6 : 1;
+  const int n_jobs = 6 * n_cells / per_job;
   std::vector<int> cell_status(n_cells, RPM_OK);
   std::mutex status_mu;
   auto worker = [&]() {
@@ -1180,7 +1232,7 @@ rpm_status rpm_effective_stiffness_batch(const rpm_cell* cells, int n_cells, con
     for (;;) {
       const int job = next.fetch_add(1);
       if (job >= n_jobs || hard_error != RPM_OK) break;
-      const int ci = job / 6, j = job % 6;
+      const int ci = job * per_job / 6;
       const rpm_cell& cl = cells[ci];
       const auto key = std::make_tuple(cl.grid.nx, cl.grid.ny, cl.grid.nz);
       rpm_ctx*& ctx = ctxs[key];
@@ -1201,20 +1253,23 @@ rpm_status rpm_effective_stiffness_batch(const rpm_cell* cells, int n_cells, con
         loaded_cell = ci;
         loaded_ctx = ctx;
       }
-      double E[6] = {0, 0, 0, 0, 0, 0};
-      E[j] = j < 3 ? 1.0 : 0.5;
-      rpm_solve_info inf{};
-      const rpm_status s = rpm_solve(ctx, E, nullptr, nullptr, nullptr, 0, &inf);
-      if (s == RPM_ERR_CUDA || s == RPM_ERR_INVALID_ARG) {
-        hard_error = s;
-        break;
+      for (int j = job * per_job % 6; j < job * per_job % 6 + per_job; ++j) {
+        double E[6] = {0, 0, 0, 0, 0, 0};
+        E[j] = j < 3 ? 1.0 : 0.5;
+        rpm_solve_info inf{};
+        const rpm_status s = rpm_solve(ctx, E, nullptr, nullptr, nullptr, 0, &inf);
+        if (s == RPM_ERR_CUDA || s == RPM_ERR_INVALID_ARG) {
+          hard_error = s;
+          break;
+        }
+        for (int i = 0; i < 6; ++i) C_eff[(size_t)ci * 36 + i * 6 + j] = inf.mean_stress[i];
+        if (info) info[(size_t)ci * 6 + j] = inf;
+        if (s != RPM_OK) {
+          std::lock_guard<std::mutex> lk(status_mu);
+          if (cell_status[ci] == RPM_OK) cell_status[ci] = s;
+        }
       }
-      for (int i = 0; i < 6; ++i) C_eff[(size_t)ci * 36 + i * 6 + j] = inf.mean_stress[i];
-      if (info) info[(size_t)ci * 6 + j] = inf;
-      if (s != RPM_OK) {
-        std::lock_guard<std::mutex> lk(status_mu);
-        if (cell_status[ci] == RPM_OK) cell_status[ci] = s;
-      }
+      if (hard_error != RPM_OK) break;
     }
     for (auto& kv : ctxs) rpm_destroy(kv.second);
     cudaStreamDestroy(st);

@@ -54,7 +54,8 @@ class rpm_options(ctypes.Structure):
                 ("warm_tol", ctypes.c_double), ("warm_c0_scale", ctypes.c_double),
                 ("warm_max_iters", ctypes.c_int), ("warm_p_max", ctypes.c_int),
                 ("warm_from_eps0", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("plane_variant", ctypes.c_int), ("pencil_variant", ctypes.c_int)]
+                ("plane_variant", ctypes.c_int), ("pencil_variant", ctypes.c_int),
+                ("share_basis", ctypes.c_int)]
 
 
 class rpm_solve_info(ctypes.Structure):
@@ -65,7 +66,7 @@ class rpm_solve_info(ctypes.Structure):
                 ("ms", ctypes.c_float), ("gamma_ms", ctypes.c_float),
                 ("proj_ms", ctypes.c_float), ("launches", ctypes.c_longlong),
                 ("proj_bytes", ctypes.c_double), ("warm_iters", ctypes.c_int),
-                ("warm_residual", ctypes.c_double)]
+                ("warm_residual", ctypes.c_double), ("basis_reused", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {"iters": self.iters, "gamma_applies": self.gamma_applies,
@@ -74,7 +75,8 @@ class rpm_solve_info(ctypes.Structure):
                 "residual0": self.residual0, "mean_stress": list(self.mean_stress),
                 "ms": self.ms, "gamma_ms": self.gamma_ms, "proj_ms": self.proj_ms,
                 "launches": self.launches, "proj_bytes": self.proj_bytes,
-                "warm_iters": self.warm_iters, "warm_residual": self.warm_residual}
+                "warm_iters": self.warm_iters, "warm_residual": self.warm_residual,
+                "basis_reused": self.basis_reused}
 
 
 class rpm_cell(ctypes.Structure):

@@ -522,3 +522,55 @@ def test_bounded_wait_gives_up_and_the_stream_stays_usable(rpm):
     with rpm.Context(cell) as ctx:
         st, info = ctx.solve(ms.unit_strain(0))
     assert st == rpm.RPM_OK and info["converged"]
+
+
+def _soft_sphere_cell(n):
+    """Centred sphere R = L/4 of E = 1e-2 in a matrix E = 1, C0 = matrix:
+    RPM needs a basis here (the basic scheme's slow modes sit near 1)."""
+    return ms._two_phase(ms.centred_sphere(n, 0.25), 1.0, 1e-2, c0_scale=1.0, name="softsphere")
+
+
+_SHARED_REF = {}
+
+
+@pytest.mark.parametrize("share", [0, 1])
+def test_effective_stiffness_shared_basis_matches_oracle(rpm, share):
+    """Block RPM (options.share_basis): F_u does not depend on the load, so
+    the six loads of C_eff can start from the unstable basis the previous
+    load left; the fixed point is the same, so C_eff matches the FP64 oracle
+    either way, and with sharing loads 2-6 report the vectors they took
+    over.  (Sharing is not faster: each unit load excites its own part of
+    the slow eigenspace, which a basis filled by the earlier loads leaves no
+    room for.)"""
+    cell = _soft_sphere_cell(24)
+    if "C" not in _SHARED_REF:
+        prob = o.Problem.from_cell(cell)
+        _SHARED_REF["C"], _ = o.effective_stiffness(prob, o.rpm_solve,
+                                                    o.Options(tol=1e-10, p_max=20))
+    C_ref = _SHARED_REF["C"]
+    opts = rpm.rpm_default_options(tol=1e-6, p_max=20, share_basis=share)
+    with rpm.Context(cell, opts) as ctx:
+        C, infos, st = ctx.effective_stiffness()
+    assert st == rpm.RPM_OK and all(i["converged"] for i in infos)
+    assert np.max(np.abs(C - C_ref)) < CEFF_TOL * np.max(np.abs(C_ref))
+    assert infos[0]["basis_reused"] == 0
+    if share:
+        assert all(i["basis_reused"] > 0 for i in infos[1:])
+    else:
+        assert all(i["basis_reused"] == 0 for i in infos)
+
+
+def test_shared_basis_is_dropped_when_the_map_changes(rpm):
+    """A stored basis belongs to one map F_u: changing C0 (or the phases or
+    materials) drops it, and the next solve starts from an empty basis."""
+    cell = _soft_sphere_cell(24)
+    E = ms.unit_strain(0)
+    opts = rpm.rpm_default_options(tol=1e-6, p_max=20, share_basis=1)
+    with rpm.Context(cell, opts) as ctx:
+        _, a = ctx.solve(E)
+        _, b = ctx.solve(E)
+        assert a["basis_size"] > 0 and b["basis_reused"] == a["basis_size"] and b["converged"]
+        rpm.rpm_set_materials(ctx.handle, list(zip(cell.lam, cell.mu)),
+                              (0.9 * cell.lam0, 0.9 * cell.mu0))
+        _, c = ctx.solve(E)
+        assert c["basis_reused"] == 0 and c["converged"]
