@@ -87,33 +87,54 @@ __device__ __forceinline__ void dots_body(const float4* __restrict__ x,
                                           const float4* __restrict__ xm,
                                           const float4* __restrict__ Y, long long ys4, int K,
                                           int row0, long long n4, double* partials, int nblk) {
+  // The thread's kPerThread difference vectors stay in registers; each basis
+  // vector is then read as kPerThread independent 16-byte loads issued
+  // together, so that many loads are in flight per thread.
   float acc[KMAX + 1];
 #pragma unroll
   for (int j = 0; j <= KMAX; ++j) acc[j] = 0.f;
   const long long total = 6 * n4;
   const long long base = (long long)blockIdx.x * kRedThreads * kPerThread + threadIdx.x;
-#pragma unroll 1
+  float4 d[kPerThread];
+  float w[kPerThread];
+#pragma unroll
   for (int r = 0; r < kPerThread; ++r) {
     const long long q = base + (long long)r * kRedThreads;
-    if (q >= total) break;
-    const float w = (q >= 3 * n4) ? 2.f : 1.f;
-    const float4 a = x[q];
-    float4 d = a;
-    if (xm) {
-      const float4 b = xm[q];
-      d = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
-    }
-    acc[0] = fmaf(w, dot4(d, d), acc[0]);
+    const bool in = q < total;
+    w[r] = in ? ((q >= 3 * n4) ? 2.f : 1.f) : 0.f;
+    d[r] = in ? x[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  if (xm) {
 #pragma unroll
-    for (int j = 0; j < KMAX; ++j) {
-      if (j < K) acc[1 + j] = fmaf(w, dot4(d, Y[j * ys4 + q]), acc[1 + j]);
+    for (int r = 0; r < kPerThread; ++r) {
+      const long long q = base + (long long)r * kRedThreads;
+      if (q < total) {
+        const float4 b = xm[q];
+        d[r] = make_float4(d[r].x - b.x, d[r].y - b.y, d[r].z - b.z, d[r].w - b.w);
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kPerThread; ++r) acc[0] = fmaf(w[r], dot4(d[r], d[r]), acc[0]);
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) {
+    if (j < K) {
+      const float4* yj = Y + j * ys4;
+      float4 y[kPerThread];
+#pragma unroll
+      for (int r = 0; r < kPerThread; ++r) {
+        const long long q = base + (long long)r * kRedThreads;
+        y[r] = q < total ? yj[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int r = 0; r < kPerThread; ++r) acc[1 + j] = fmaf(w[r], dot4(d[r], y[r]), acc[1 + j]);
     }
   }
   block_store<KMAX + 1>(acc, K + 1, row0, partials, nblk);
 }
 
 template <int KMAX>
-__global__ void __launch_bounds__(kRedThreads) k_dots(const float4* __restrict__ x,
+__global__ void __launch_bounds__(kRedThreads, 2) k_dots(const float4* __restrict__ x,
                                                       const float4* __restrict__ xm,
                                                       const float4* __restrict__ Y, long long ys4,
                                                       int K, int row0, long long n4,
@@ -127,7 +148,7 @@ __global__ void __launch_bounds__(kRedThreads) k_dots(const float4* __restrict__
 // of k_newton with p = K.  The ticket counter is zero between launches (the
 // last block resets it).  One launch instead of three.
 template <int KMAX>
-__global__ void __launch_bounds__(kRedThreads) k_dots_fused(
+__global__ void __launch_bounds__(kRedThreads, 2) k_dots_fused(
     const float4* __restrict__ x, const float4* __restrict__ xm, const float4* __restrict__ Y,
     long long ys4, int K, long long n4, double* partials, int nblk, double* sums,
     unsigned int* ticket, const double* __restrict__ M, double* c, double* res_out,
