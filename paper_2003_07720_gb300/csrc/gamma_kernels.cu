@@ -667,7 +667,9 @@ __device__ __forceinline__ float post_shear(float e, float b, float4 pm, float m
 // bulk asynchronous copy; y step 1 packs the DC and Nyquist x columns as
 // X_0 + i X_nx/2 (their inverse y transforms are real, so the result holds
 // both in its real and imaginary parts); the tangling is fused into x step
-// 1; x step 2 writes the real rows to global memory, scaled.
+// 1; x step 2 writes the real rows to global memory, scaled.  Without POST
+// a non-null `eps` is a field added to the output on the way out (the
+// defect of a re-centred iterate).
 //
 // POST: the pass ends with Algorithm 3's post-step instead (Section 5.5),
 // the transformed planes being eps_b and `eps` the map's input.  Blocks are
@@ -839,18 +841,26 @@ __global__ void __launch_bounds__(kPlaneThreads, kPlaneMinBlocks)
     float2 ev[X1];   // shear post-step: the map's input and phases, loaded ahead
     uchar2 pv[X1];   // of the transform where the registers allow
     constexpr bool AHEAD = X1 <= 8;
-    if (POST && AHEAD && !gather) {
+    const bool addend = !POST && eps != nullptr;
+    if ((POST || addend) && AHEAD && !gather) {
 #pragma unroll
       for (int i = 0; i < X1; ++i) {
         ev[i] = e2[c * nf2 + r + i * X2];
-        pv[i] = ph2[r + i * X2];
+        if (POST) pv[i] = ph2[r + i * X2];
       }
     }
     float2 v[X1];
 #pragma unroll
     for (int i = 0; i < X1; ++i) v[i] = p[i * X2];
     RegDft<X1, true>::run(v);
-    if (!POST) {   // -> global
+    if (!POST && addend) {   // -> global, with the added field
+#pragma unroll
+      for (int i = 0; i < X1; ++i) {
+        if (!AHEAD) ev[i] = e2[c * nf2 + r + i * X2];
+        const float2 b = cscale(v[i], scale);
+        out2[c * nf2 + r + i * X2] = make_float2(b.x + ev[i].x, b.y + ev[i].y);
+      }
+    } else if (!POST) {   // -> global
 #pragma unroll
       for (int i = 0; i < X1; ++i) out2[c * nf2 + r + i * X2] = cscale(v[i], scale);
     } else if (gather) {   // -> the block's own slots, for the cluster's post-step
@@ -1567,7 +1577,8 @@ static cudaError_t launch_ypencil(const GridDev& g, float2* spec, bool inv, cuda
 
 template <int NX>
 static cudaError_t launch_fused_plane(const GridDev& g, const float* in, float* out, float2* spec,
-                                      int mode, int which, cudaStream_t st) {
+                                      int mode, int which, cudaStream_t st,
+                                      const float* add = nullptr) {
   constexpr int NXH = NX / 2, SX = NXH + 1;
   const size_t tab = (size_t)(NXH + NX + SX) * sizeof(float2);
   const size_t smem = (size_t)NX * SX * sizeof(float2) + tab;
@@ -1579,8 +1590,7 @@ static cudaError_t launch_fused_plane(const GridDev& g, const float* in, float* 
   }
   if ((e = set_smem(k_plane_inv<NX, NX, false>, smem)) != cudaSuccess) return e;
   return launch_pdl(k_plane_inv<NX, NX, false>, dim3(6 * g.nz), kPlaneThreads, smem, st, g,
-                    (const float2*)spec, out, 1.0f / (float)g.n, (const float*)nullptr,
-                    (const float4*)nullptr);
+                    (const float2*)spec, out, 1.0f / (float)g.n, add, (const float4*)nullptr);
 }
 
 // pass C with Algorithm 3's post-step (clusters of three blocks)
@@ -1629,10 +1639,11 @@ static bool fused_pencil_ok(int nz) {
 }
 
 static cudaError_t dispatch_fused_plane(const GridDev& g, const float* in, float* out,
-                                        float2* spec, int mode, int which, cudaStream_t st) {
+                                        float2* spec, int mode, int which, cudaStream_t st,
+                                        const float* add = nullptr) {
   switch (g.nx) {
 #define RPM_CASE(N) \
-  case N: return launch_fused_plane<N>(g, in, out, spec, mode, which, st);
+  case N: return launch_fused_plane<N>(g, in, out, spec, mode, which, st, add);
     RPM_FUSED_PLANE_SIZES(RPM_CASE)
 #undef RPM_CASE
     default: return cudaErrorInvalidValue;
@@ -1807,27 +1818,40 @@ cudaError_t launch_polarization_map(const GridDev& g, const float4* post, const 
   return launch_polarization_post(g, post, in, eb, out, st);
 }
 
+// the added field rides on the fused last pass (float2 accesses)
+static bool fused_add_ok(const GridDev& g, const float* out, const float* add,
+                         const float2* spec) {
+  return plane_path(g, spec) == 0 && ((uintptr_t)out & 7) == 0 && ((uintptr_t)add & 7) == 0;
+}
+
+int gamma_add_launches(const GridDev& g, const float* out, const float* add, const float2* spec) {
+  return gamma_launches(g) + (add && !fused_add_ok(g, out, add, spec) ? 1 : 0);
+}
+
 cudaError_t launch_apply_gamma(const GridDev& g, const float* in, float* out, float2* spec,
-                               const double E[6], int mode, cudaStream_t st) {
+                               const double E[6], int mode, cudaStream_t st, const float* add) {
   const GammaArgs ga = gamma_args(g, E);
   cudaError_t e;
   auto zpass = [&]() { return z_pass(g, spec, mode, ga, st); };
   const int path = plane_path(g, spec);
-  if (path == 0) {
+  if (path == 0 && (!add || fused_add_ok(g, out, add, spec))) {
     if ((e = dispatch_fused_plane(g, in, out, spec, mode, 0, st)) != cudaSuccess) return e;
     if ((e = zpass()) != cudaSuccess) return e;
-    return dispatch_fused_plane(g, in, out, spec, mode, 1, st);
+    return dispatch_fused_plane(g, in, out, spec, mode, 1, st, add);
   }
-  if (path == 1) {
+  if (path <= 1 && plane_fits(g.nx, g.ny)) {
     if ((e = dispatch_plane(g, in, out, spec, mode, 0, st)) != cudaSuccess) return e;
     if ((e = zpass()) != cudaSuccess) return e;
-    return dispatch_plane(g, in, out, spec, mode, 1, st);
+    e = dispatch_plane(g, in, out, spec, mode, 1, st);
+  } else {
+    if ((e = dispatch_rows(g, in, out, spec, mode, 0, st)) != cudaSuccess) return e;
+    if ((e = dispatch_ypencil(g, spec, false, st)) != cudaSuccess) return e;
+    if ((e = zpass()) != cudaSuccess) return e;
+    if ((e = dispatch_ypencil(g, spec, true, st)) != cudaSuccess) return e;
+    e = dispatch_rows(g, in, out, spec, mode, 1, st);
   }
-  if ((e = dispatch_rows(g, in, out, spec, mode, 0, st)) != cudaSuccess) return e;
-  if ((e = dispatch_ypencil(g, spec, false, st)) != cudaSuccess) return e;
-  if ((e = zpass()) != cudaSuccess) return e;
-  if ((e = dispatch_ypencil(g, spec, true, st)) != cudaSuccess) return e;
-  return dispatch_rows(g, in, out, spec, mode, 1, st);
+  if (e != cudaSuccess || !add) return e;
+  return launch_axpby(out, 1.f, out, 1.f, add, g.n, st);
 }
 
 }  // namespace rpm

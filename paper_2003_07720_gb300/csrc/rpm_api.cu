@@ -298,10 +298,11 @@ struct Ops {
   void done(size_t i) {
     if (i != (size_t)-1) cudaEventRecord(c->prof_ev[2 * i + 1], c->st);
   }
-  bool gamma(const float* in, float* out, const double* E, int mode) {
+  bool gamma(const float* in, float* out, const double* E, int mode, const float* add = nullptr) {
     const size_t m = mark(0);
-    c->launches += gamma_launches(c->g);
-    const bool ok = ck(c, launch_apply_gamma(c->g, in, out, c->spec, E, mode, c->st), "apply_gamma");
+    c->launches += gamma_add_launches(c->g, out, add, c->spec);
+    const bool ok =
+        ck(c, launch_apply_gamma(c->g, in, out, c->spec, E, mode, c->st, add), "apply_gamma");
     done(m);
     return ok;
   }
@@ -784,6 +785,8 @@ rpm_status solve_impl(rpm_ctx* c, const double E[6], const float* eps0, float* e
   int rebases = 0;
   auto step_map = [&](const float* in, float* out) -> bool {
     if (!based) return ops.fmap(in, out, E, false);
+    // Eq. 3.9: the defect is added in the map's last pass
+    if (o.scheme == RPM_SCHEME_BASIC) return ops.gamma(in, out, nullptr, GM_LINEAR, defect);
     if (!ops.fmap(in, out, nullptr, true)) return false;
     ++c->launches;
     return ck(c, launch_axpby(out, 1.f, out, 1.f, defect, c->n, c->st), "defect");

@@ -44,9 +44,13 @@ struct GridDev {
 
 // One Gamma0 application: in [6][n] -> out [6][n] through the spectrum
 // scratch spec [6][nz][plane] (float2).  E (6 tensor components) is only
-// used in GM_FULL_MAP.  Returns a CUDA error code.
+// used in GM_FULL_MAP.  A non-null `add` [6][n] is added to the output (in
+// the last pass where the fused kernels run, else by one more launch).
+// Returns a CUDA error code.
 cudaError_t launch_apply_gamma(const GridDev& g, const float* in, float* out, float2* spec,
-                               const double E[6], int mode, cudaStream_t st);
+                               const double E[6], int mode, cudaStream_t st,
+                               const float* add = nullptr);
+int gamma_add_launches(const GridDev& g, const float* out, const float* add, const float2* spec);
 
 // Algorithm 3 as one map application: eps_b = the Gamma0 map of `in` under g
 // (whose material table holds s_b's moduli, E = Eb), then the post-step
