@@ -89,10 +89,10 @@ __device__ __forceinline__ void dots_body(const float4* __restrict__ x,
                                           int row0, long long n4, double* partials, int nblk) {
   // The thread's kPerThread difference vectors stay in registers; each basis
   // vector is then read as kPerThread independent 16-byte loads issued
-  // together, so that many loads are in flight per thread.
-  float acc[KMAX + 1];
-#pragma unroll
-  for (int j = 0; j <= KMAX; ++j) acc[j] = 0.f;
+  // together, and its warp sum is taken at once (no accumulator stays live
+  // across the vectors, which keeps the register count at three blocks per SM).
+  __shared__ double red[kRedThreads / 32][KMAX + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long total = 6 * n4;
   const long long base = (long long)blockIdx.x * kRedThreads * kPerThread + threadIdx.x;
   float4 d[kPerThread];
@@ -114,8 +114,13 @@ __device__ __forceinline__ void dots_body(const float4* __restrict__ x,
       }
     }
   }
+  {
+    float a = 0.f, hi, lo;
 #pragma unroll
-  for (int r = 0; r < kPerThread; ++r) acc[0] = fmaf(w[r], dot4(d[r], d[r]), acc[0]);
+    for (int r = 0; r < kPerThread; ++r) a = fmaf(w[r], dot4(d[r], d[r]), a);
+    warp_sum_compensated(a, hi, lo);
+    if (lane == 0) red[warp][0] = (double)hi + (double)lo;
+  }
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) {
     if (j < K) {
@@ -126,15 +131,25 @@ __device__ __forceinline__ void dots_body(const float4* __restrict__ x,
         const long long q = base + (long long)r * kRedThreads;
         y[r] = q < total ? yj[q] : make_float4(0.f, 0.f, 0.f, 0.f);
       }
+      float a = 0.f, hi, lo;
 #pragma unroll
-      for (int r = 0; r < kPerThread; ++r) acc[1 + j] = fmaf(w[r], dot4(d[r], y[r]), acc[1 + j]);
+      for (int r = 0; r < kPerThread; ++r) a = fmaf(w[r], dot4(d[r], y[r]), a);
+      warp_sum_compensated(a, hi, lo);
+      if (lane == 0) red[warp][1 + j] = (double)hi + (double)lo;
     }
   }
-  block_store<KMAX + 1>(acc, K + 1, row0, partials, nblk);
+  __syncthreads();
+  for (int j = threadIdx.x; j <= K; j += blockDim.x) {
+    if (j == 0 && row0 != 0) continue;
+    double t = 0.0;
+#pragma unroll
+    for (int v = 0; v < kRedThreads / 32; ++v) t += red[v][j];
+    partials[(size_t)(j == 0 ? 0 : row0 + j) * nblk + blockIdx.x] = t;
+  }
 }
 
 template <int KMAX>
-__global__ void __launch_bounds__(kRedThreads, 2) k_dots(const float4* __restrict__ x,
+__global__ void __launch_bounds__(kRedThreads, 3) k_dots(const float4* __restrict__ x,
                                                       const float4* __restrict__ xm,
                                                       const float4* __restrict__ Y, long long ys4,
                                                       int K, int row0, long long n4,
@@ -148,7 +163,7 @@ __global__ void __launch_bounds__(kRedThreads, 2) k_dots(const float4* __restric
 // of k_newton with p = K.  The ticket counter is zero between launches (the
 // last block resets it).  One launch instead of three.
 template <int KMAX>
-__global__ void __launch_bounds__(kRedThreads, 2) k_dots_fused(
+__global__ void __launch_bounds__(kRedThreads, 3) k_dots_fused(
     const float4* __restrict__ x, const float4* __restrict__ xm, const float4* __restrict__ Y,
     long long ys4, int K, long long n4, double* partials, int nblk, double* sums,
     unsigned int* ticket, const double* __restrict__ M, double* c, double* res_out,
