@@ -451,10 +451,11 @@ void rpm_destroy(rpm_ctx* c) {
 
 rpm_status rpm_set_phase(rpm_ctx* c, const uint8_t* phase, int on_device) {
   if (!c || !phase) return fail(c, RPM_ERR_INVALID_ARG, "null argument");
-  if (!on_device) {
-    for (long long i = 0; i < c->n; ++i)
-      if (phase[i] >= c->phases.size())
-        return fail(c, RPM_ERR_INVALID_ARG, "phase id out of range");
+  if (!on_device) {   // largest id by a branch-free (vectorisable) reduction
+    uint8_t mx = 0;
+    for (long long i = 0; i < c->n; ++i) mx = phase[i] > mx ? phase[i] : mx;
+    if (c->n > 0 && mx >= c->phases.size())
+      return fail(c, RPM_ERR_INVALID_ARG, "phase id out of range");
   }
   if (!ck(c, cudaMemcpyAsync(c->phase, phase, (size_t)c->n,
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st),

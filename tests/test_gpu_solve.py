@@ -574,3 +574,20 @@ def test_shared_basis_is_dropped_when_the_map_changes(rpm):
                               (0.9 * cell.lam0, 0.9 * cell.mu0))
         _, c = ctx.solve(E)
         assert c["basis_reused"] == 0 and c["converged"]
+
+
+def test_host_phase_map_with_an_unknown_id_is_refused(rpm):
+    """A host phase map is checked before upload: an id at or above the
+    number of phases (here in the last voxel) is RPM_ERR_INVALID_ARG and the
+    context keeps its previous map."""
+    cell = ms.cell_sphere32(16)
+    E = ms.unit_strain(0)
+    with rpm.Context(cell) as ctx:
+        _, ref = ctx.solve(E)
+        bad = cell.phase.copy()
+        bad.reshape(-1)[-1] = 2
+        with pytest.raises(rpm.RpmError) as ei:
+            rpm.rpm_set_phase(ctx.handle, bad)
+        assert ei.value.status == rpm.RPM_ERR_INVALID_ARG
+        _, again = ctx.solve(E)
+        assert again["mean_stress"] == ref["mean_stress"]
