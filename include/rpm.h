@@ -99,7 +99,7 @@ typedef struct {
                             whole-plane kernels where the plane fits (nx = ny <= 128),
                             else as 2; 2 the five-pass row and y-pencil kernels */
   int pencil_variant;    /* z pass: 0 (default) the fused register-resident kernel where
-                            the grid has it (nz 32-128), else the default tile; 1 half,
+                            the grid has it (nz 32, 48, 96, 128), else the default tile; 1 half,
                             2 twice the default pencils per block; 3 the default tile */
   int share_basis;       /* 1: a solve starts from the unstable basis (Z, W = F_u Z, H)
                             that an earlier solve of the same map left in the context --

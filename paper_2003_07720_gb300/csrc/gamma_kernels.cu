@@ -219,13 +219,13 @@ struct GammaArgs {
 };
 
 // T consecutive (ky, kx) pencils per pass-B block: TT = 0 takes the default
-// for the length (8 pencils = 64-byte rows at nz = 128; 16 at nz = 256, one
-// 512-thread block per SM, measured 0.980 vs 1.012 ms per 256^3 apply with
-// 8); the tile autotuner of rpm_create also tries half and twice the
-// default (GridDev::pencil_t).
+// for the length (8 pencils = 64-byte rows at nz = 64 and 128; 16 at
+// nz = 256, one 512-thread block per SM, measured 0.980 vs 1.012 ms per
+// 256^3 apply with 8); the tile autotuner of rpm_create also tries half and
+// twice the default (GridDev::pencil_t).
 template <int NZ, int TT = 0>
 struct PencilCfg {
-  static constexpr int T = TT ? TT : (NZ >= 256 ? 16 : (NZ >= 128 ? 8 : (NZ >= 64 ? 16 : 32)));
+  static constexpr int T = TT ? TT : (NZ >= 256 ? 16 : (NZ >= 64 ? 8 : 32));
   static constexpr int NZP = (NZ % 2 == 0) ? NZ + 1 : NZ;
 };
 
@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(2 * kThreads, 2) k_pass_b_wide(GridDev g,
 
 // ---------------------------------------------------------------------------
 // Fused-step kernels (square planes nx = ny in {48, 64, 96, 128}; pencils of
-// length nz with 128 / split_n1(nz) pencils per block, nz in {32 .. 128}).
+// length nz with 128 / split_n1(nz) pencils per block, nz in {32, 48, 96, 128}).
 // ---------------------------------------------------------------------------
 
 // Row task q of an x step over NY rows: (y, n2).  With N2 = 8 the two
@@ -1573,7 +1573,9 @@ static cudaError_t launch_ypencil(const GridDev& g, float2* spec, bool inv, cuda
 // the fused plane passes: nx = ny with a two-step x split of nx/2 and an even
 // first factor; the fused pencil pass: 128 / split_n1(nz) pencils per block
 #define RPM_FUSED_PLANE_SIZES(X) X(48) X(64) X(96) X(128)
-#define RPM_FUSED_Z_SIZES(X) X(32) X(48) X(64) X(96) X(128)
+// (nz = 64 takes the 8-pencil tile of the original z pass: 0.0293 vs
+// 0.0314 ms per 64^3 apply)
+#define RPM_FUSED_Z_SIZES(X) X(32) X(48) X(96) X(128)
 
 template <int NX>
 static cudaError_t launch_fused_plane(const GridDev& g, const float* in, float* out, float2* spec,

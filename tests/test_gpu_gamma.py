@@ -55,7 +55,7 @@ def _run(cell, mode, nyq=0, seed=1, E=None):
                                    (48, 48, 48), (96, 96, 96), (12, 24, 24), (6, 12, 12),
                                    (3, 48, 48), (24, 6, 6), (16, 96, 48), (8, 96, 256),
                                    # fused plane and pencil kernels (square planes 48-128,
-                                   # nz 32-128), alone and with the original ones
+                                   # nz 32, 48, 96, 128), alone and with the original ones
                                    (128, 64, 64), (64, 96, 96), (32, 128, 128), (48, 64, 64),
                                    (128, 48, 48), (96, 32, 64), (64, 128, 128), (6, 96, 96),
                                    (256, 48, 48), (256, 16, 32)])
