@@ -72,6 +72,29 @@ def test_host_side_checks(L):
     assert L.rpm_status_string(5) == b"RPM_ERR_NOT_CONVERGED"
 
 
+def test_variant_profile_and_basis_options_are_checked_on_the_host(L):
+    """Defaults of the kernel-variant, profiling and shared-basis options,
+    and their range checks before any device work; the queries and the
+    bounded-wait self-check refuse null arguments."""
+    from paper_2003_07720_gb300 import rpm
+    o = rpm.rpm_default_options()
+    assert (o.autotune, o.plane_variant, o.pencil_variant, o.share_basis, o.profile) == \
+        (0, 0, 0, 0, 0)
+    h = ctypes.c_void_p()
+    g = rpm.rpm_grid(16, 16, 16, 1.0, 1.0, 1.0)
+    iso = (rpm.rpm_iso * 1)(rpm.rpm_iso(1.0, 1.0))
+    ph = (ctypes.c_uint8 * (16 ** 3))()
+    for field, value in (("plane_variant", 3), ("pencil_variant", 4), ("share_basis", 2),
+                         ("profile", -1), ("autotune", 2)):
+        bad = rpm.rpm_default_options(**{field: value})
+        st = L.rpm_create(ctypes.byref(g), ctypes.cast(ph, ctypes.c_void_p), 0, 1, iso,
+                          rpm.rpm_iso(1.0, 1.0), ctypes.byref(bad), None, ctypes.byref(h))
+        assert st == rpm.RPM_ERR_INVALID_ARG and not h.value, field
+    assert L.rpm_plane_variant(None) == -1
+    assert L.rpm_pencil_tile(None) == 0
+    assert L.rpm_bounded_wait_check(None, None, None) == rpm.RPM_ERR_INVALID_ARG
+
+
 def test_fno_host_side_checks(L):
     import ctypes as ct
     from paper_2003_07720_gb300 import fno
