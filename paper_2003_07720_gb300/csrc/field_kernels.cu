@@ -9,6 +9,8 @@
 // grid reductions run in float64 with a fixed order (deterministic).
 #include <math.h>
 
+#include <atomic>
+
 #include "rpm_internal.h"
 
 namespace rpm {
@@ -337,13 +339,39 @@ static int stream_blocks(long long total4) {
   return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
+// Grid of a grid-stride kernel: the blocks that are resident at once (so no
+// partial last wave), at most one block per 256 threads' worth of work.
+// (the occupancy query runs once per kernel instance: `slot` caches it)
+template <typename Kern>
+static int resident_grid(Kern kernel, long long total4, std::atomic<int>& slot) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0, v = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    sms = v;
+  }
+  int per_sm = slot.load();
+  if (per_sm < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kRedThreads, 0) !=
+            cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    slot.store(per_sm);
+  }
+  const long long want = (total4 + kRedThreads - 1) / kRedThreads;
+  const long long cap = (long long)sms * per_sm;
+  return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+static std::atomic<int> g_combine_occ[4];   // resident blocks per SM of k_combine<2, 8, 16, 32>
+
 cudaError_t launch_combine(float* out, const float* x, float xscale, const float* Y,
                            long long ystride, int K, const double* coef, float cscale,
                            long long n, cudaStream_t st) {
   const long long total4 = 6 * (n / 4);
   float4* o4 = reinterpret_cast<float4*>(out);
   const long long ys4 = ystride / 4;
-  const int blocks = stream_blocks(total4);
   // K > 32: the first chunk forms xs * x + ..., later chunks accumulate into out
   for (int k0 = 0; k0 == 0 || k0 < K; k0 += 32) {
     const int Kc = K - k0 < 32 ? K - k0 : 32;
@@ -352,13 +380,17 @@ cudaError_t launch_combine(float* out, const float* x, float xscale, const float
     const float4* y4 = reinterpret_cast<const float4*>(Y) + (Y ? k0 * ys4 : 0);
     const double* cf = coef ? coef + k0 : nullptr;
     if (Kc <= 2)
-      k_combine<2><<<blocks, kRedThreads, 0, st>>>(o4, x4, xs, y4, ys4, Kc, cf, cscale, total4);
+      k_combine<2><<<resident_grid(k_combine<2>, total4, g_combine_occ[0]), kRedThreads, 0, st>>>(
+          o4, x4, xs, y4, ys4, Kc, cf, cscale, total4);
     else if (Kc <= 8)
-      k_combine<8><<<blocks, kRedThreads, 0, st>>>(o4, x4, xs, y4, ys4, Kc, cf, cscale, total4);
+      k_combine<8><<<resident_grid(k_combine<8>, total4, g_combine_occ[1]), kRedThreads, 0, st>>>(
+          o4, x4, xs, y4, ys4, Kc, cf, cscale, total4);
     else if (Kc <= 16)
-      k_combine<16><<<blocks, kRedThreads, 0, st>>>(o4, x4, xs, y4, ys4, Kc, cf, cscale, total4);
+      k_combine<16><<<resident_grid(k_combine<16>, total4, g_combine_occ[2]), kRedThreads, 0, st>>>(
+          o4, x4, xs, y4, ys4, Kc, cf, cscale, total4);
     else
-      k_combine<32><<<blocks, kRedThreads, 0, st>>>(o4, x4, xs, y4, ys4, Kc, cf, cscale, total4);
+      k_combine<32><<<resident_grid(k_combine<32>, total4, g_combine_occ[3]), kRedThreads, 0, st>>>(
+          o4, x4, xs, y4, ys4, Kc, cf, cscale, total4);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
